@@ -1,0 +1,42 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle's callers.
+
+This module only draws random numbers; it holds none of the method's arithmetic.
+The paper's molecules (and their PySCF integrals) are not available, so random
+molecule-shaped inputs stand in for them:
+
+  * one-electron integrals h_pq ~ N(0, 1), symmetrised as (h + h^T) / 2;
+  * two-electron integrals (pq|rs) ~ N(0, 0.1) (standard deviation 0.1), averaged
+    over the 8 index permutations of real orbitals so the 8-fold symmetry holds;
+  * UCCSD amplitudes theta ~ N(0, 0.05) (standard deviation 0.05).
+"""
+import numpy as np
+
+
+def random_integrals(n_spatial, seed):
+    rng = np.random.default_rng(seed)
+    h = rng.normal(0.0, 1.0, size=(n_spatial, n_spatial))
+    h = 0.5 * (h + h.T)
+    g = rng.normal(0.0, 0.1, size=(n_spatial,) * 4)
+    g = (g + g.transpose(1, 0, 2, 3) + g.transpose(0, 1, 3, 2) + g.transpose(1, 0, 3, 2)
+         + g.transpose(2, 3, 0, 1) + g.transpose(3, 2, 0, 1) + g.transpose(2, 3, 1, 0)
+         + g.transpose(3, 2, 1, 0)) / 8.0
+    return np.ascontiguousarray(h), np.ascontiguousarray(g)
+
+
+def random_amplitudes(n_params, seed):
+    rng = np.random.default_rng(10_000 + seed)
+    return rng.normal(0.0, 0.05, size=n_params)
+
+
+def h2_shaped_integrals(seed):
+    """Two spatial orbitals with only the integrals a real H2-like molecule has:
+    h_11, h_22, (11|11), (22|22), (11|22) and the (12|12)-class exchange."""
+    rng = np.random.default_rng(seed)
+    h = np.diag(rng.normal(0.0, 1.0, size=2))
+    g = np.zeros((2, 2, 2, 2))
+    g[0, 0, 0, 0], g[1, 1, 1, 1] = rng.normal(0.5, 0.1, size=2)
+    g[0, 0, 1, 1] = g[1, 1, 0, 0] = rng.normal(0.5, 0.1)
+    x = rng.normal(0.2, 0.05)
+    for idx in [(0, 1, 0, 1), (1, 0, 1, 0), (0, 1, 1, 0), (1, 0, 0, 1)]:
+        g[idx] = x
+    return h, g
