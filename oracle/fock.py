@@ -94,3 +94,30 @@ def hf_energy(h, eri, n_electrons, e_core=0.0):
             if i % 2 == j % 2:
                 e -= 0.5 * eri[i // 2, j // 2, j // 2, i // 2]
     return e
+
+
+def operator_matrix(n, ops):
+    """Dense matrix of a product of ladder operators [(p, dagger), ...] (leftmost first)."""
+    pc = _popcount_table(n)
+    dim = 2 ** n
+    basis = np.arange(dim, dtype=np.int64)
+    st, a = basis.copy(), np.ones(dim)
+    for p, dag in reversed(ops):
+        st, a = (_create if dag else _annihilate)(st, a, p, pc)
+    out = np.zeros((dim, dim))
+    nz = a != 0
+    np.add.at(out, (st[nz], basis[nz]), a[nz])
+    return out
+
+
+def number_operator(n):
+    pc = _popcount_table(n)
+    return np.diag(pc.astype(float))
+
+
+def sz2_operator(n):
+    """2 S_z = N_alpha - N_beta (alpha on even qubits)."""
+    b = np.arange(2 ** n)
+    alpha = sum(((b >> q) & 1) for q in range(0, n, 2))
+    beta = sum(((b >> q) & 1) for q in range(1, n, 2))
+    return np.diag((alpha - beta).astype(float))

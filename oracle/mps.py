@@ -127,3 +127,23 @@ def to_statevector(mps):
     c = t[:, 0]                                     # index = sum_k i_k 2^(n-1-k)
     n = mps.n
     return c.reshape((2,) * n).transpose(tuple(range(n))[::-1]).reshape(-1)
+
+
+def from_statevector(psi, n):
+    """Exact right-canonical MPS of a dense state by right-to-left SVDs (no truncation
+    beyond exact zeros); lam holds the exact Schmidt numbers of each bond."""
+    c = psi.reshape((2,) * n).transpose(tuple(range(n))[::-1]).reshape(-1)  # site 0 slowest
+    B = [None] * n
+    lam = [None] * (n - 1)
+    cur = c.reshape(-1, 2)          # (left configurations, i_{n-1}) with right bond 1
+    r_right = 1
+    for k in range(n - 1, 0, -1):
+        mat = cur.reshape(-1, 2 * r_right)
+        U, s, Vh = np.linalg.svd(mat, full_matrices=False)
+        r = int(np.count_nonzero(s > 1e-14 * s[0]))
+        B[k] = Vh[:r].reshape(r, 2, r_right)
+        lam[k - 1] = s[:r] / np.linalg.norm(s[:r])
+        cur = U[:, :r] * s[:r]
+        r_right = r
+    B[0] = cur.reshape(1, 2, r_right)
+    return MPS(B, lam)
