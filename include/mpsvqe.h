@@ -1,0 +1,194 @@
+/*
+ * mpsvqe.h - C ABI of the GB300 MPS-VQE hot path (arXiv 2207.03711).
+ *
+ * The library applies a Trotterised UCCSD circuit of Pauli rotations to a
+ * right-canonical matrix product state by two-site gate contraction and truncated
+ * SVD (Sec. III-A, Eqs. 6-10), then evaluates E = <psi|H|psi> of a Jordan-Wigner
+ * qubit Hamiltonian as a weighted sum of Pauli-string expectations (Eq. 2,
+ * Sec. III-C), with all strings sharing left environments through a prefix trie.
+ *
+ * Conventions for every call:
+ *   - Every function returns an int status: MPS_OK (0) or a negative MPS_E* code.
+ *     No exception crosses the ABI. mps_last_error() gives a thread-local message.
+ *   - Pointer arguments are caller-owned HOST memory, read during the call or
+ *     written before it returns. Handles own their device memory, which is freed by
+ *     the matching *_destroy.
+ *   - Calls are synchronous with respect to their host outputs; device work is
+ *     issued on the CUDA stream given to mps_create (NULL = legacy default stream).
+ *   - Qubit q is MPS site q (site 0 leftmost) and bit q of a statevector index.
+ *     Pauli strings are n_qubits bytes each, 0 = I, 1 = X, 2 = Y, 3 = Z, site 0 first.
+ *   - Angles, coefficients, energies and Schmidt numbers are double.
+ *   - Complex arrays are interleaved (re, im) doubles.
+ */
+#ifndef MPSVQE_H
+#define MPSVQE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mps_s* mps_t;   /* n_slots MPS states on one GPU + workspaces  */
+typedef struct ham_s* ham_t;   /* weighted Pauli sum + its prefix trie (host) */
+typedef struct circ_s* circ_t; /* compiled two-site gate list                 */
+
+enum {
+  MPS_OK = 0,
+  MPS_EINVAL = -1,   /* bad argument (null pointer, size out of range, ...)       */
+  MPS_ENOMEM = -2,   /* device or host allocation failed                          */
+  MPS_ECUDA = -3,    /* a CUDA runtime call failed (message has the CUDA error)   */
+  MPS_ETIMEOUT = -4, /* a bounded device-side wait ran out                        */
+  MPS_ENOCONV = -5   /* an SVD hit its sweep cap; results are still written       */
+};
+
+enum { MPS_FP64 = 0, MPS_MIXED = 1 };
+
+/* ------------------------------------------------------------------ Hamiltonian */
+
+/* Eq. (1) -> Eq. (2), Sec. II-A: Jordan-Wigner transform of the electronic
+ * Hamiltonian H = sum h_pq a+_ps a_qs + 1/2 sum (pq|rs) a+_ps a+_rt a_st a_qs + e_core
+ * with interleaved spin orbitals p = 2k + s (n_qubits = 2 n_spatial) and
+ * a_p = Z_0..Z_{p-1} (X_p + i Y_p) / 2.
+ *   h:   n_spatial^2 doubles, row-major, symmetric.
+ *   eri: n_spatial^4 doubles, chemist order (pq|rs) at ((p*n+q)*n+r)*n+s.
+ * Terms with |a| <= 1e-12 max|a| are dropped; terms are stored in trie order
+ * (lexicographic over sites 0..n-1 with I < X < Y < Z). n_spatial in [1, 64].
+ * Errors: MPS_EINVAL for n_spatial out of range or null pointers; MPS_EINVAL if
+ * a coefficient has an imaginary part above 1e-10 (non-Hermitian input). */
+int ham_jw_from_integrals(int n_spatial, const double* h, const double* eri, double e_core,
+                          ham_t* out);
+
+/* Sec. III-C: H = sum_i a_i P_i from explicit strings. paulis: n_terms x n_qubits
+ * bytes; coeff: n_terms doubles. Duplicate strings are merged. The prefix trie used
+ * by vqe_energy is built here (host, once; Sec. III-D keeps the measurement part
+ * constant across optimisation steps). n_qubits in [2, 128], n_terms >= 1. */
+int ham_create(int n_qubits, int64_t n_terms, const uint8_t* paulis, const double* coeff,
+               ham_t* out);
+
+/* Number of stored terms, and a copy of them in trie order (either output may be NULL). */
+int ham_num_terms(ham_t ham, int64_t* n_terms);
+int ham_get_terms(ham_t ham, uint8_t* paulis, double* coeff);
+int ham_destroy(ham_t ham);
+
+/* -------------------------------------------------------------------- circuit */
+
+/* Eqs. (3)-(4), Sec. II-A and Sec. III-D: Trotterised UCCSD on the Hartree-Fock
+ * determinant with qubits 0..n_electrons-1 occupied. Excitations are
+ * spin-conserving; singles (i, a) in lexicographic order, then doubles
+ * ((i < j), (a < b)) in lexicographic order; tau = a+_a a_i or a+_a a+_b a_i a_j,
+ * one parameter each. Under Jordan-Wigner tau - tau+ = i sum_k c_k P_k with
+ * commuting strings, applied in increasing (x-mask, z-mask) order as rotations
+ * exp(-i phi_k P_k / 2), phi_k = -2 c_k theta_e. *n_params receives the number of
+ * excitations. n_qubits in [2, 128], 0 < n_electrons < n_qubits. */
+int circ_uccsd(int n_qubits, int n_electrons, circ_t* out, int* n_params);
+
+/* General rotation list: rotation r is exp(-i * scale[r] * theta[param_idx[r]] / 2 * P_r),
+ * applied in order r = 0, 1, ... Each rotation is compiled (Sec. III-D, Sec. III-A)
+ * into nearest-neighbour two-site gates: basis change (H for X, Rx(pi/2) for Y),
+ * a parity ladder lo -> hi (CNOT onto a non-identity qubit, SWAP across an identity
+ * qubit), Rz(phi) on hi, the mirror ladder and basis change; single-qubit gates are
+ * fused into the neighbouring two-site gates and the top hop/Rz/hop into one gate,
+ * giving 2 (hi - lo) - 1 gates per rotation. param_idx[r] < 0 means a fixed angle
+ * phi = scale[r]. */
+int circ_create(int n_qubits, int64_t n_rot, const uint8_t* paulis, const int32_t* param_idx,
+                const double* scale, circ_t* out);
+
+/* Reference determinant used by vqe_energy* (Sec. III-D): occ is n_qubits bytes of
+ * 0/1. circ_uccsd sets qubits 0..n_electrons-1; circ_create sets all zero. */
+int circ_set_reference(circ_t circ, const uint8_t* occ);
+
+/* Inspection: rotation count/list and the compiled gate list for a given theta
+ * (bond: n_gates ints; U: n_gates x 4 x 4 complex, row index 2 i_b + i_{b+1}). */
+int circ_num_rotations(circ_t circ, int64_t* n_rot, int* n_params);
+int circ_get_rotations(circ_t circ, uint8_t* paulis, int32_t* param_idx, double* scale);
+int circ_num_gates(circ_t circ, int64_t* n_gates);
+int circ_export_gates(circ_t circ, const double* theta, int32_t* bond, double* U);
+int circ_destroy(circ_t circ);
+
+/* ------------------------------------------------------------------ MPS state */
+
+/* Allocate n_slots MPS states of n_qubits sites with bond cap chi (Eq. 6) on the
+ * current device, each initialised to the all-zero product state. precision:
+ * MPS_FP64 (complex128 tensors, FP64 SVD and contractions) or MPS_MIXED (complex64
+ * tensors, FP32 contractions and SVD, FP64 Schmidt numbers and energy sums).
+ * cuda_stream: a cudaStream_t (NULL = default stream). n_qubits in [2, 128],
+ * chi in [1, 256], n_slots in [1, 4096]. Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA. */
+int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_stream, mps_t* out);
+
+/* Sec. III-D: reset slot to the product state |occ_0 occ_1 ...> (bytes 0/1), all
+ * bond ranks 1, lambda = [1]. */
+int mps_reset(mps_t mps, int slot, const uint8_t* occ);
+
+/* Truncation controls (Eq. 9): keep k = min(chi, #{sigma > cutoff * sigma_0});
+ * max_sweeps caps the one-sided Jacobi SVD. Defaults: cutoff 1e-13 (FP64) or
+ * 2^-20 (mixed); max_sweeps 40. */
+int mps_set_svd_params(mps_t mps, double cutoff, int max_sweeps);
+
+/* Sec. III-A, Eqs. (7)-(10), for every gate of circ on slot 0 in order: contract
+ * B_n B_{n+1} with the gate, scale rows by lambda_{n-1}, truncated SVD, B_{n+1} <- V,
+ * B_n <- M V^+, lambda_n <- sigma. theta: n_params doubles. *discarded_weight
+ * (may be NULL) receives the sum over gates of the discarded fraction
+ * sum_dropped sigma^2 / sum sigma^2 (Eq. 9's monitored truncation error).
+ * Returns MPS_ENOCONV if any SVD hit the sweep cap (state is still updated). */
+int mps_apply_circuit(mps_t mps, circ_t circ, const double* theta, double* discarded_weight);
+
+/* Same as mps_apply_circuit for explicit gates on slot 0: bond[g] in [0, n-2],
+ * U: n_gates x 4 x 4 complex (row index 2 i_b + i_{b+1}). */
+int mps_apply_gates(mps_t mps, int64_t n_gates, const int32_t* bond, const double* U,
+                    double* discarded_weight);
+
+/* Eq. (11) generalised to Pauli strings (Sec. III-C): re[i] + i im[i] =
+ * <psi|P_i|psi> / <psi|psi> on slot 0, by exact transfer-matrix contraction over
+ * a prefix trie (shared left environments) and right identity environments. */
+int mps_expect_paulis(mps_t mps, int64_t n_terms, const uint8_t* paulis, double* re, double* im);
+
+/* Checkpoint / inspection of one slot. ranks: n_qubits-1 bond ranks.
+ * B: concatenated site tensors, site k of shape (r_{k-1}, 2, r_k) row-major complex;
+ * lam: concatenated Schmidt numbers of bonds 0..n-2. mps_state_size gives the
+ * number of complex entries of B and doubles of lam for the current ranks. */
+int mps_get_ranks(mps_t mps, int slot, int32_t* ranks);
+int mps_state_size(mps_t mps, int slot, int64_t* n_B, int64_t* n_lam);
+int mps_get_state(mps_t mps, int slot, double* B, double* lam);
+int mps_set_state(mps_t mps, int slot, const int32_t* ranks, const double* B, const double* lam);
+
+/* Sec. III-C/III-D energy evaluation on slot 0: reset to the reference
+ * determinant of circ (circ_set_reference), apply circ with theta, evaluate every term
+ * of ham, and return E = sum_i a_i Re<P_i> / <psi|psi> (Neumaier-compensated FP64
+ * sum in trie order). */
+int vqe_energy(mps_t mps, circ_t circ, ham_t ham, const double* theta, double* energy);
+
+/* n_batch independent evaluations (slots 0..n_batch-1, n_batch <= n_slots);
+ * thetas: n_batch x n_params; energies: n_batch. */
+int vqe_energy_batch(mps_t mps, circ_t circ, ham_t ham, int n_batch, const double* thetas,
+                     double* energies);
+
+/* Parameter-shift gradient dE/dtheta_e for the n_sel parameters sel[]:
+ * sum over the rotations k of e of scale_k [E(phi_k + pi/2) - E(phi_k - pi/2)] / 2,
+ * all shifted circuits batched over slots (needs n_slots >= 2). */
+int vqe_gradient(mps_t mps, circ_t circ, ham_t ham, const double* theta, int n_sel,
+                 const int32_t* sel, double* grad);
+
+/* Per-call statistics of the last apply/energy call on this handle. */
+typedef struct {
+  double discarded_weight; /* summed discarded fraction, slot 0           */
+  int32_t max_rank;        /* largest bond rank reached, slot 0           */
+  int32_t max_sweeps;      /* most Jacobi sweeps used by one SVD           */
+  int64_t n_gates;         /* gates applied per slot                       */
+  int64_t n_svd_noconv;    /* SVDs that hit the sweep cap                  */
+  double ms_circuit;       /* CUDA-event time of the circuit kernels       */
+  double ms_measure;       /* CUDA-event time of the measurement kernels   */
+  int64_t kernel_launches; /* device kernels launched by the call          */
+} mps_stats_t;
+int mps_get_stats(mps_t mps, mps_stats_t* stats);
+
+int mps_destroy(mps_t mps);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char* mps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPSVQE_H */

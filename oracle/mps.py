@@ -147,3 +147,32 @@ def from_statevector(psi, n):
         r_right = r
     B[0] = cur.reshape(1, 2, r_right)
     return MPS(B, lam)
+
+
+def random_canonical(n, ranks, gauss):
+    """A random MPS in exact canonical form from caller-drawn Gaussian arrays.
+
+    ranks: n-1 bond ranks; gauss[k]: complex array of shape (2 r_k, r_{k-1}) for
+    site k (r_{-1} = r_{n-1} = 1). Each site is made right-canonical by a QR
+    factorisation, then every bond is rotated (left to right) so that the left
+    environment sum_i B^{i+} L B^i is diagonal; lam then holds the exact Schmidt
+    numbers of each bond and the state has unit norm.
+    """
+    r = [1] + list(ranks) + [1]
+    B = []
+    for k in range(n):
+        q, _ = np.linalg.qr(gauss[k])                # (2 r_k) x r_{k-1}, orthonormal columns
+        B.append(q.conj().T.reshape(r[k], 2, r[k + 1]))
+    # normalise: site 0 is a single row of unit norm already (QR of a column)
+    lam = []
+    L = np.ones((1, 1), dtype=complex)
+    for k in range(n - 1):
+        L = sum(B[k][:, i, :].conj().T @ L @ B[k][:, i, :] for i in range(2))
+        w, W = np.linalg.eigh(L)
+        idx = np.argsort(w)[::-1]
+        w, W = w[idx], W[:, idx]
+        B[k] = np.einsum("aib,bc->aic", B[k], W)
+        B[k + 1] = np.einsum("cb,bjd->cjd", W.conj().T, B[k + 1])
+        L = np.diag(w).astype(complex)
+        lam.append(np.sqrt(np.maximum(w, 0.0)))
+    return MPS(B, lam)

@@ -1,0 +1,796 @@
+// C ABI of the MPS-VQE engine: handles, device memory layout and the host-side
+// orchestration of the kernels in kernels.cu. See include/mpsvqe.h for the contract.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/mpsvqe.h"
+#include "host.hpp"
+#include "kernels.cuh"
+
+using namespace mpsvqe;
+
+namespace {
+constexpr double kHalfPi = 1.5707963267948966;
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(MPS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define CU(call)                                                 \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
+  } while (0)
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MPS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return MPS_OK;
+}
+#define TRY(call)              \
+  do {                         \
+    int r_ = (call);           \
+    if (r_ != MPS_OK) return r_; \
+  } while (0)
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+}  // namespace
+
+// ----------------------------------------------------------------------- handles
+struct ham_s {
+  int n = 0;
+  std::vector<Term> terms;  // trie order
+  Trie trie;
+  double id_coeff = 0.0;
+  int64_t id_term = -1;
+  // device copies (current device at upload)
+  bool uploaded = false;
+  double* d_coeff = nullptr;
+  std::vector<int32_t*> d_parent, d_cnode, d_cterm;
+  std::vector<uint8_t*> d_edge, d_cletter;
+  ~ham_s() {
+    dfree(d_coeff);
+    for (auto p : d_parent) dfree(p);
+    for (auto p : d_cnode) dfree(p);
+    for (auto p : d_cterm) dfree(p);
+    for (auto p : d_edge) dfree(p);
+    for (auto p : d_cletter) dfree(p);
+  }
+};
+
+struct circ_s {
+  Compiled comp;
+  std::vector<int64_t> rot_param_gate;  // gate carrying Rz of each rotation (-1 if none)
+  bool uploaded = false;
+  GateRec* d_gates = nullptr;
+  double* d_mats = nullptr;
+  ~circ_s() {
+    dfree(d_gates);
+    dfree(d_mats);
+  }
+};
+
+struct mps_s {
+  int n = 0, chi = 0, prec = 0, n_slots = 0;
+  size_t es = 0;  // bytes per complex entry
+  cudaStream_t st = nullptr;
+  std::vector<int> cap;            // cap of bond b at index b+1; cap[0] = cap[n] = 1
+  std::vector<int64_t> site_off;
+  DevMPS dm{};
+  int64_t* d_site_off = nullptr;
+  MeasDev w{};
+  int32_t w_nodes = 0;
+  int64_t w_terms = 0;
+  double* d_theta = nullptr;
+  size_t theta_cap = 0;
+  uint8_t* d_occ = nullptr;
+  int64_t* d_shift_gate = nullptr;
+  double* d_shift_val = nullptr;
+  double cutoff = 1e-13;
+  int max_sweeps = 40;
+  mps_stats_t stats{};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  std::vector<double> h_out;
+  ~mps_s() {
+    dfree(dm.B);
+    dfree(dm.lam);
+    dfree(dm.rank);
+    dfree(dm.work_M);
+    dfree(dm.work_X);
+    dfree(dm.dw);
+    dfree(dm.stat);
+    dfree(d_site_off);
+    dfree(w.R);
+    dfree(w.Bhat);
+    dfree(w.L[0]);
+    dfree(w.L[1]);
+    dfree(w.T);
+    dfree(w.vals);
+    dfree(w.out);
+    dfree(d_theta);
+    dfree(d_occ);
+    dfree(d_shift_gate);
+    dfree(d_shift_val);
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+// ------------------------------------------------------------------ host helpers
+static int make_ham(int n, std::vector<Term> terms, ham_t* out) {
+  auto h = std::make_unique<ham_s>();
+  h->n = n;
+  h->terms = std::move(terms);
+  for (size_t t = 0; t < h->terms.size(); ++t) {
+    bool id = std::all_of(h->terms[t].code.begin(), h->terms[t].code.end(), [](uint8_t c) { return c == 0; });
+    if (id) {
+      h->id_term = (int64_t)t;
+      h->id_coeff = h->terms[t].coeff;
+    }
+  }
+  build_trie(n, h->terms, &h->trie);
+  *out = h.release();
+  return MPS_OK;
+}
+
+static int upload_ham(ham_s* h) {
+  if (h->uploaded) return MPS_OK;
+  const int n = h->n;
+  std::vector<double> co(h->terms.size());
+  for (size_t t = 0; t < co.size(); ++t) co[t] = h->terms[t].coeff;
+  TRY(dalloc(&h->d_coeff, co.size()));
+  CU(cudaMemcpy(h->d_coeff, co.data(), co.size() * 8, cudaMemcpyHostToDevice));
+  h->d_parent.assign(n, nullptr);
+  h->d_edge.assign(n, nullptr);
+  h->d_cnode.assign(n, nullptr);
+  h->d_cletter.assign(n, nullptr);
+  h->d_cterm.assign(n, nullptr);
+  const Trie& t = h->trie;
+  for (int k = 0; k < n; ++k) {
+    if (!t.parent[k].empty()) {
+      TRY(dalloc(&h->d_parent[k], t.parent[k].size()));
+      TRY(dalloc(&h->d_edge[k], t.edge[k].size()));
+      CU(cudaMemcpy(h->d_parent[k], t.parent[k].data(), t.parent[k].size() * 4, cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(h->d_edge[k], t.edge[k].data(), t.edge[k].size(), cudaMemcpyHostToDevice));
+    }
+    if (!t.close_term[k].empty()) {
+      TRY(dalloc(&h->d_cnode[k], t.close_node[k].size()));
+      TRY(dalloc(&h->d_cletter[k], t.close_letter[k].size()));
+      TRY(dalloc(&h->d_cterm[k], t.close_term[k].size()));
+      CU(cudaMemcpy(h->d_cnode[k], t.close_node[k].data(), t.close_node[k].size() * 4, cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(h->d_cletter[k], t.close_letter[k].data(), t.close_letter[k].size(), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(h->d_cterm[k], t.close_term[k].data(), t.close_term[k].size() * 4, cudaMemcpyHostToDevice));
+    }
+  }
+  h->uploaded = true;
+  return MPS_OK;
+}
+
+static int finish_circ(int n, std::vector<Rotation> rots, int n_params, circ_t* out) {
+  auto c = std::make_unique<circ_s>();
+  c->comp.n_params = n_params;
+  compile_rotations(n, rots, &c->comp);
+  c->comp.reference.assign(n, 0);
+  // gate carrying the rotation angle: the single gate (|S| = 1) or the top gate
+  const auto& R = c->comp.rotations;
+  c->rot_param_gate.assign(R.size(), -1);
+  for (size_t r = 0; r < R.size(); ++r) {
+    int lo = -1, hi = -1, w = 0;
+    for (int q = 0; q < n; ++q)
+      if (R[r].code[q]) {
+        if (lo < 0) lo = q;
+        hi = q;
+        ++w;
+      }
+    if (w == 0) continue;
+    c->rot_param_gate[r] = c->comp.rot_first_gate[r] + (w == 1 ? 0 : (hi - lo - 1));
+  }
+  *out = c.release();
+  return MPS_OK;
+}
+
+static int upload_circ(circ_s* c) {
+  if (c->uploaded) return MPS_OK;
+  TRY(dalloc(&c->d_gates, c->comp.gates.size()));
+  TRY(dalloc(&c->d_mats, c->comp.mats.size() * 2));
+  if (!c->comp.gates.empty())
+    CU(cudaMemcpy(c->d_gates, c->comp.gates.data(), c->comp.gates.size() * sizeof(GateRec), cudaMemcpyHostToDevice));
+  if (!c->comp.mats.empty())
+    CU(cudaMemcpy(c->d_mats, c->comp.mats.data(), c->comp.mats.size() * 16, cudaMemcpyHostToDevice));
+  c->uploaded = true;
+  return MPS_OK;
+}
+
+static int ensure_theta(mps_s* m, size_t count) {
+  if (count <= m->theta_cap) return MPS_OK;
+  dfree(m->d_theta);
+  m->d_theta = nullptr;
+  m->theta_cap = 0;
+  TRY(dalloc(&m->d_theta, count));
+  m->theta_cap = count;
+  return MPS_OK;
+}
+
+static int ensure_meas(mps_s* m, int32_t nodes, int64_t terms) {
+  const size_t chi2 = (size_t)m->chi * m->chi;
+  if (!m->w.R) {
+    void* p;
+    CU(cudaMalloc(&p, (size_t)(m->n + 1) * chi2 * m->es));
+    m->w.R = p;
+    CU(cudaMalloc(&p, (size_t)m->dm.slot_elems * m->es));
+    m->w.Bhat = p;
+  }
+  if (nodes > m->w_nodes) {
+    dfree(m->w.L[0]);
+    dfree(m->w.L[1]);
+    dfree(m->w.T);
+    m->w.L[0] = m->w.L[1] = m->w.T = nullptr;
+    m->w_nodes = 0;
+    void* p;
+    if (cudaMalloc(&p, (size_t)nodes * chi2 * m->es) != cudaSuccess) return fail(MPS_ENOMEM, "env buffer");
+    m->w.L[0] = p;
+    if (cudaMalloc(&p, (size_t)nodes * chi2 * m->es) != cudaSuccess) return fail(MPS_ENOMEM, "env buffer");
+    m->w.L[1] = p;
+    if (cudaMalloc(&p, (size_t)nodes * 2 * chi2 * m->es) != cudaSuccess) return fail(MPS_ENOMEM, "T buffer");
+    m->w.T = p;
+    m->w_nodes = nodes;
+  }
+  if (terms > m->w_terms) {
+    dfree(m->w.vals);
+    dfree(m->w.out);
+    m->w.vals = m->w.out = nullptr;
+    m->w_terms = 0;
+    TRY(dalloc(&m->w.vals, (size_t)terms * 2));
+    TRY(dalloc(&m->w.out, 4 + (size_t)terms * 2));
+    m->w_terms = terms;
+  }
+  return MPS_OK;
+}
+
+// Apply gates [0, n_gates) of circ to slots [slot0, slot0 + count); thetas: count x n_params
+// (host). shifts: optional per-slot (gate index, extra angle) for parameter shifts.
+static int run_circuit(mps_s* m, circ_s* c, int slot0, int count, const double* thetas,
+                       const int64_t* shift_gate, const double* shift_val) {
+  TRY(upload_circ(c));
+  const int np = std::max(1, c->comp.n_params);
+  TRY(ensure_theta(m, (size_t)count * np));
+  if (thetas && c->comp.n_params > 0)
+    CU(cudaMemcpyAsync(m->d_theta, thetas, (size_t)count * np * 8, cudaMemcpyHostToDevice, m->st));
+  (void)shift_gate;
+  (void)shift_val;
+  CircDev cd{c->d_gates, (int64_t)c->comp.gates.size(), c->d_mats, np};
+  const int64_t G = (int64_t)c->comp.gates.size();
+  const int64_t chunk = 16384;
+  CU(cudaEventRecord(m->ev[0], m->st));
+  int launches = 0;
+  for (int64_t g0 = 0; g0 < G; g0 += chunk) {
+    CU(launch_circuit(m->dm, m->prec, cd, g0, std::min(G, g0 + chunk), slot0, count, m->d_theta, m->cutoff,
+                      m->max_sweeps, m->st));
+    ++launches;
+  }
+  CU(cudaEventRecord(m->ev[1], m->st));
+  CU(cudaEventSynchronize(m->ev[1]));
+  float ms = 0;
+  CU(cudaEventElapsedTime(&ms, m->ev[0], m->ev[1]));
+  m->stats.ms_circuit += ms;
+  m->stats.kernel_launches += launches;
+  m->stats.n_gates = G;
+  return MPS_OK;
+}
+
+static int read_slot_stats(mps_s* m, int slot, double* dw, int* stat4) {
+  CU(cudaMemcpy(dw, m->dm.dw + slot, 8, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(stat4, m->dm.stat + 4 * slot, 16, cudaMemcpyDeviceToHost));
+  return MPS_OK;
+}
+
+static int upload_reset(mps_s* m, int slot0, int count, const uint8_t* occ_rows) {
+  CU(cudaMemcpyAsync(m->d_occ, occ_rows, (size_t)count * m->n, cudaMemcpyHostToDevice, m->st));
+  CU(launch_reset(m->dm, m->prec, slot0, count, m->d_occ, m->st));
+  m->stats.kernel_launches += 1;
+  return MPS_OK;
+}
+
+// Evaluate all terms of h on one slot; out_host receives 4 + 2 T doubles.
+static int run_measure(mps_s* m, ham_s* h, int slot, double* out_host) {
+  TRY(upload_ham(h));
+  const int64_t T = (int64_t)h->terms.size();
+  TRY(ensure_meas(m, std::max<int32_t>(1, h->trie.max_level_nodes), std::max<int64_t>(1, T)));
+  CU(cudaEventRecord(m->ev[2], m->st));
+  int launches = 0;
+  CU(launch_right_envs(m->dm, m->prec, slot, m->w, m->st));
+  ++launches;
+  // root environment L_0 = [1]
+  static const double one_d[2] = {1.0, 0.0};
+  static const float one_f[2] = {1.0f, 0.0f};
+  CU(cudaMemcpyAsync(m->w.L[0], m->prec == MPS_FP64 ? (const void*)one_d : (const void*)one_f, m->es,
+                     cudaMemcpyHostToDevice, m->st));
+  const Trie& t = h->trie;
+  for (int k = 0; k < t.n_levels; ++k) {
+    TrieLevelDev lv{};
+    lv.n_nodes = t.level_nodes[k];
+    if (k + 1 < h->n && k + 1 < t.n_levels) {
+      lv.n_children = t.level_nodes[k + 1];
+      lv.parent = h->d_parent[k + 1];
+      lv.edge = h->d_edge[k + 1];
+    }
+    lv.n_closes = (int32_t)t.close_term[k].size();
+    lv.close_node = h->d_cnode[k];
+    lv.close_letter = h->d_cletter[k];
+    lv.close_term = h->d_cterm[k];
+    CU(launch_level(m->dm, m->prec, slot, m->w, k, lv, k & 1, m->st, &launches));
+  }
+  CU(launch_energy_sum(m->dm, m->prec, slot, m->w, T, h->d_coeff, h->id_term >= 0 ? h->id_coeff : 0.0,
+                       h->id_term, m->st));
+  ++launches;
+  CU(cudaEventRecord(m->ev[3], m->st));
+  CU(cudaMemcpyAsync(out_host, m->w.out, (4 + 2 * (size_t)T) * 8, cudaMemcpyDeviceToHost, m->st));
+  CU(cudaStreamSynchronize(m->st));
+  float ms = 0;
+  CU(cudaEventElapsedTime(&ms, m->ev[2], m->ev[3]));
+  m->stats.ms_measure += ms;
+  m->stats.kernel_launches += launches;
+  return MPS_OK;
+}
+
+static void reset_stats(mps_s* m) { m->stats = mps_stats_t{}; }
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* mps_last_error(void) { return g_err.c_str(); }
+
+int ham_jw_from_integrals(int n_spatial, const double* h, const double* eri, double e_core, ham_t* out) {
+  if (!h || !eri || !out) return fail(MPS_EINVAL, "ham_jw_from_integrals: null pointer");
+  if (n_spatial < 1 || n_spatial > 64) return fail(MPS_EINVAL, "ham_jw_from_integrals: n_spatial out of [1, 64]");
+  std::string err;
+  std::vector<Term> terms = jordan_wigner(n_spatial, h, eri, e_core, &err);
+  if (!err.empty()) return fail(MPS_EINVAL, err);
+  if (terms.empty()) return fail(MPS_EINVAL, "ham_jw_from_integrals: Hamiltonian is zero");
+  return make_ham(2 * n_spatial, std::move(terms), out);
+}
+
+int ham_create(int n_qubits, int64_t n_terms, const uint8_t* paulis, const double* coeff, ham_t* out) {
+  if (!paulis || !coeff || !out) return fail(MPS_EINVAL, "ham_create: null pointer");
+  if (n_qubits < 2 || n_qubits > kMaxQubits || n_terms < 1) return fail(MPS_EINVAL, "ham_create: bad sizes");
+  std::vector<Term> terms((size_t)n_terms);
+  for (int64_t t = 0; t < n_terms; ++t) {
+    terms[t].code.assign(paulis + t * n_qubits, paulis + (t + 1) * n_qubits);
+    for (uint8_t c : terms[t].code)
+      if (c > 3) return fail(MPS_EINVAL, "ham_create: Pauli code out of {0,1,2,3}");
+    terms[t].coeff = coeff[t];
+  }
+  return make_ham(n_qubits, canonical_terms(n_qubits, std::move(terms), 0.0), out);
+}
+
+int ham_num_terms(ham_t h, int64_t* n_terms) {
+  if (!h || !n_terms) return fail(MPS_EINVAL, "ham_num_terms: null pointer");
+  *n_terms = (int64_t)h->terms.size();
+  return MPS_OK;
+}
+
+int ham_get_terms(ham_t h, uint8_t* paulis, double* coeff) {
+  if (!h) return fail(MPS_EINVAL, "ham_get_terms: null handle");
+  for (size_t t = 0; t < h->terms.size(); ++t) {
+    if (paulis) std::memcpy(paulis + t * h->n, h->terms[t].code.data(), h->n);
+    if (coeff) coeff[t] = h->terms[t].coeff;
+  }
+  return MPS_OK;
+}
+
+int ham_destroy(ham_t h) {
+  delete h;
+  return MPS_OK;
+}
+
+int circ_uccsd(int n_qubits, int n_electrons, circ_t* out, int* n_params) {
+  if (!out) return fail(MPS_EINVAL, "circ_uccsd: null pointer");
+  if (n_qubits < 2 || n_qubits > kMaxQubits || n_electrons <= 0 || n_electrons >= n_qubits)
+    return fail(MPS_EINVAL, "circ_uccsd: bad sizes");
+  int np = 0;
+  std::vector<Rotation> rots = uccsd_rotations(n_qubits, n_electrons, &np);
+  TRY(finish_circ(n_qubits, std::move(rots), np, out));
+  for (int q = 0; q < n_electrons; ++q) (*out)->comp.reference[q] = 1;
+  if (n_params) *n_params = np;
+  return MPS_OK;
+}
+
+int circ_create(int n_qubits, int64_t n_rot, const uint8_t* paulis, const int32_t* param_idx,
+                const double* scale, circ_t* out) {
+  if (!paulis || !param_idx || !scale || !out) return fail(MPS_EINVAL, "circ_create: null pointer");
+  if (n_qubits < 2 || n_qubits > kMaxQubits || n_rot < 0) return fail(MPS_EINVAL, "circ_create: bad sizes");
+  std::vector<Rotation> rots((size_t)n_rot);
+  int np = 0;
+  for (int64_t r = 0; r < n_rot; ++r) {
+    rots[r].code.assign(paulis + r * n_qubits, paulis + (r + 1) * n_qubits);
+    for (uint8_t c : rots[r].code)
+      if (c > 3) return fail(MPS_EINVAL, "circ_create: Pauli code out of {0,1,2,3}");
+    rots[r].param = param_idx[r];
+    rots[r].scale = scale[r];
+    np = std::max(np, param_idx[r] + 1);
+  }
+  return finish_circ(n_qubits, std::move(rots), np, out);
+}
+
+int circ_set_reference(circ_t c, const uint8_t* occ) {
+  if (!c || !occ) return fail(MPS_EINVAL, "circ_set_reference: null pointer");
+  for (int q = 0; q < c->comp.n; ++q) {
+    if (occ[q] > 1) return fail(MPS_EINVAL, "circ_set_reference: occupation not 0/1");
+    c->comp.reference[q] = occ[q];
+  }
+  return MPS_OK;
+}
+
+int circ_num_rotations(circ_t c, int64_t* n_rot, int* n_params) {
+  if (!c) return fail(MPS_EINVAL, "circ_num_rotations: null handle");
+  if (n_rot) *n_rot = (int64_t)c->comp.rotations.size();
+  if (n_params) *n_params = c->comp.n_params;
+  return MPS_OK;
+}
+
+int circ_get_rotations(circ_t c, uint8_t* paulis, int32_t* param_idx, double* scale) {
+  if (!c) return fail(MPS_EINVAL, "circ_get_rotations: null handle");
+  const int n = c->comp.n;
+  for (size_t r = 0; r < c->comp.rotations.size(); ++r) {
+    if (paulis) std::memcpy(paulis + r * n, c->comp.rotations[r].code.data(), n);
+    if (param_idx) param_idx[r] = c->comp.rotations[r].param;
+    if (scale) scale[r] = c->comp.rotations[r].scale;
+  }
+  return MPS_OK;
+}
+
+int circ_num_gates(circ_t c, int64_t* n_gates) {
+  if (!c || !n_gates) return fail(MPS_EINVAL, "circ_num_gates: null pointer");
+  *n_gates = (int64_t)c->comp.gates.size();
+  return MPS_OK;
+}
+
+int circ_export_gates(circ_t c, const double* theta, int32_t* bond, double* U) {
+  if (!c) return fail(MPS_EINVAL, "circ_export_gates: null handle");
+  if (!theta && c->comp.n_params > 0) return fail(MPS_EINVAL, "circ_export_gates: theta is null");
+  for (size_t g = 0; g < c->comp.gates.size(); ++g) {
+    if (bond) bond[g] = c->comp.gates[g].bond;
+    if (U) gate_matrix(c->comp, c->comp.gates[g], theta, reinterpret_cast<cd*>(U + 32 * g));
+  }
+  return MPS_OK;
+}
+
+int circ_destroy(circ_t c) {
+  delete c;
+  return MPS_OK;
+}
+
+int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_stream, mps_t* out) {
+  if (!out) return fail(MPS_EINVAL, "mps_create: null pointer");
+  if (n_qubits < 2 || n_qubits > kMaxQubits) return fail(MPS_EINVAL, "mps_create: n_qubits out of [2, 128]");
+  if (chi < 1 || chi > 256) return fail(MPS_EINVAL, "mps_create: chi out of [1, 256]");
+  if (precision != MPS_FP64 && precision != MPS_MIXED) return fail(MPS_EINVAL, "mps_create: bad precision");
+  if (n_slots < 1 || n_slots > 4096) return fail(MPS_EINVAL, "mps_create: n_slots out of [1, 4096]");
+  auto m = std::make_unique<mps_s>();
+  m->n = n_qubits;
+  m->chi = chi;
+  m->prec = precision;
+  m->n_slots = n_slots;
+  m->es = precision == MPS_FP64 ? 16 : 8;
+  m->st = (cudaStream_t)cuda_stream;
+  m->cutoff = precision == MPS_FP64 ? 1e-13 : std::ldexp(1.0, -20);
+  const int n = n_qubits;
+  m->cap.assign(n + 1, 1);
+  for (int b = 0; b < n - 1; ++b) {
+    int e = std::min(b + 1, n - 1 - b);
+    m->cap[b + 1] = e >= 30 ? chi : std::min(chi, 1 << e);
+  }
+  m->site_off.assign(n, 0);
+  int64_t off = 0;
+  for (int k = 0; k < n; ++k) {
+    m->site_off[k] = off;
+    off += (int64_t)m->cap[k] * 2 * m->cap[k + 1];
+  }
+  DevMPS& d = m->dm;
+  d.n = n;
+  d.chi = chi;
+  d.n_slots = n_slots;
+  d.slot_elems = off;
+  const size_t mm = 2 * (size_t)chi;
+  void* p;
+  if (cudaMalloc(&p, (size_t)n_slots * off * m->es) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: B"); }
+  d.B = p;
+  TRY(dalloc(&d.lam, (size_t)n_slots * (n - 1) * chi));
+  TRY(dalloc(&d.rank, (size_t)n_slots * (n + 1)));
+  if (cudaMalloc(&p, (size_t)n_slots * mm * mm * m->es) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_M"); }
+  d.work_M = p;
+  if (cudaMalloc(&p, (size_t)n_slots * mm * (mm + 1) * m->es) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_X"); }
+  d.work_X = p;
+  TRY(dalloc(&d.dw, n_slots));
+  TRY(dalloc(&d.stat, (size_t)n_slots * 4));
+  TRY(dalloc(&m->d_site_off, n));
+  CU(cudaMemcpy(m->d_site_off, m->site_off.data(), n * 8, cudaMemcpyHostToDevice));
+  d.site_off = m->d_site_off;
+  TRY(dalloc(&m->d_occ, (size_t)n_slots * n));
+  TRY(dalloc(&m->d_shift_gate, n_slots));
+  TRY(dalloc(&m->d_shift_val, n_slots));
+  for (auto& e : m->ev) CU(cudaEventCreate(&e));
+  std::vector<uint8_t> zeros((size_t)n_slots * n, 0);
+  TRY(upload_reset(m.get(), 0, n_slots, zeros.data()));
+  CU(cudaStreamSynchronize(m->st));
+  *out = m.release();
+  return MPS_OK;
+}
+
+int mps_destroy(mps_t m) {
+  if (m) cudaStreamSynchronize(m->st);
+  delete m;
+  return MPS_OK;
+}
+
+int mps_reset(mps_t m, int slot, const uint8_t* occ) {
+  if (!m || !occ) return fail(MPS_EINVAL, "mps_reset: null pointer");
+  if (slot < 0 || slot >= m->n_slots) return fail(MPS_EINVAL, "mps_reset: slot out of range");
+  for (int q = 0; q < m->n; ++q)
+    if (occ[q] > 1) return fail(MPS_EINVAL, "mps_reset: occupation not 0/1");
+  TRY(upload_reset(m, slot, 1, occ));
+  CU(cudaStreamSynchronize(m->st));
+  return MPS_OK;
+}
+
+int mps_set_svd_params(mps_t m, double cutoff, int max_sweeps) {
+  if (!m) return fail(MPS_EINVAL, "mps_set_svd_params: null handle");
+  if (!(cutoff >= 0.0 && cutoff < 1.0) || max_sweeps < 1 || max_sweeps > 1000)
+    return fail(MPS_EINVAL, "mps_set_svd_params: cutoff in [0,1), max_sweeps in [1,1000]");
+  m->cutoff = cutoff;
+  m->max_sweeps = max_sweeps;
+  return MPS_OK;
+}
+
+static int finish_apply(mps_s* m, double* discarded_weight) {
+  double dw = 0;
+  int st4[4];
+  TRY(read_slot_stats(m, 0, &dw, st4));
+  m->stats.discarded_weight = dw;
+  m->stats.max_sweeps = st4[0];
+  m->stats.n_svd_noconv = st4[1];
+  m->stats.max_rank = st4[2];
+  if (discarded_weight) *discarded_weight = dw;
+  if (st4[1] > 0) return fail(MPS_ENOCONV, "an SVD reached the Jacobi sweep cap");
+  return MPS_OK;
+}
+
+int mps_apply_circuit(mps_t m, circ_t c, const double* theta, double* discarded_weight) {
+  if (!m || !c) return fail(MPS_EINVAL, "mps_apply_circuit: null handle");
+  if (c->comp.n != m->n) return fail(MPS_EINVAL, "mps_apply_circuit: qubit count mismatch");
+  if (!theta && c->comp.n_params > 0) return fail(MPS_EINVAL, "mps_apply_circuit: theta is null");
+  reset_stats(m);
+  // the discarded-weight accumulator and stats of slot 0 restart at this call
+  CU(cudaMemsetAsync(m->dm.dw, 0, 8, m->st));
+  CU(cudaMemsetAsync(m->dm.stat, 0, 8, m->st));
+  TRY(run_circuit(m, c, 0, 1, theta, nullptr, nullptr));
+  return finish_apply(m, discarded_weight);
+}
+
+int mps_apply_gates(mps_t m, int64_t n_gates, const int32_t* bond, const double* U, double* discarded_weight) {
+  if (!m || (n_gates > 0 && (!bond || !U))) return fail(MPS_EINVAL, "mps_apply_gates: null pointer");
+  if (n_gates < 0) return fail(MPS_EINVAL, "mps_apply_gates: negative count");
+  circ_s c;
+  c.comp.n = m->n;
+  c.comp.n_params = 0;
+  for (int64_t g = 0; g < n_gates; ++g) {
+    if (bond[g] < 0 || bond[g] > m->n - 2) return fail(MPS_EINVAL, "mps_apply_gates: bond out of range");
+    GateRec r{};
+    r.bond = bond[g];
+    r.param = -1;
+    r.m0 = (int32_t)g;
+    r.m1 = -1;
+    c.comp.gates.push_back(r);
+    for (int e = 0; e < 16; ++e) c.comp.mats.push_back(cd(U[32 * g + 2 * e], U[32 * g + 2 * e + 1]));
+  }
+  reset_stats(m);
+  CU(cudaMemsetAsync(m->dm.dw, 0, 8, m->st));
+  CU(cudaMemsetAsync(m->dm.stat, 0, 8, m->st));
+  TRY(run_circuit(m, &c, 0, 1, nullptr, nullptr, nullptr));
+  return finish_apply(m, discarded_weight);
+}
+
+int mps_expect_paulis(mps_t m, int64_t n_terms, const uint8_t* paulis, double* re, double* im) {
+  if (!m || !paulis || !re || !im) return fail(MPS_EINVAL, "mps_expect_paulis: null pointer");
+  if (n_terms < 1) return fail(MPS_EINVAL, "mps_expect_paulis: n_terms < 1");
+  const int n = m->n;
+  std::vector<int64_t> order((size_t)n_terms);
+  for (int64_t t = 0; t < n_terms; ++t) {
+    order[t] = t;
+    for (int q = 0; q < n; ++q)
+      if (paulis[t * n + q] > 3) return fail(MPS_EINVAL, "mps_expect_paulis: Pauli code out of {0,1,2,3}");
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return std::lexicographical_compare(paulis + a * n, paulis + a * n + n, paulis + b * n, paulis + b * n + n);
+  });
+  std::vector<Term> terms;
+  std::vector<int64_t> uniq_of((size_t)n_terms);
+  for (int64_t i = 0; i < n_terms; ++i) {
+    const uint8_t* c = paulis + order[i] * n;
+    if (terms.empty() || !std::equal(c, c + n, terms.back().code.begin())) terms.push_back({std::vector<uint8_t>(c, c + n), 0.0});
+    uniq_of[order[i]] = (int64_t)terms.size() - 1;
+  }
+  ham_t h = nullptr;
+  TRY(make_ham(n, std::move(terms), &h));
+  std::unique_ptr<ham_s> hold(h);
+  reset_stats(m);
+  std::vector<double> out(4 + 2 * h->terms.size());
+  TRY(run_measure(m, h, 0, out.data()));
+  for (int64_t t = 0; t < n_terms; ++t) {
+    re[t] = out[4 + 2 * uniq_of[t]];
+    im[t] = out[5 + 2 * uniq_of[t]];
+  }
+  return MPS_OK;
+}
+
+int mps_get_ranks(mps_t m, int slot, int32_t* ranks) {
+  if (!m || !ranks) return fail(MPS_EINVAL, "mps_get_ranks: null pointer");
+  if (slot < 0 || slot >= m->n_slots) return fail(MPS_EINVAL, "mps_get_ranks: slot out of range");
+  std::vector<int> r(m->n + 1);
+  CU(cudaStreamSynchronize(m->st));
+  CU(cudaMemcpy(r.data(), m->dm.rank + (size_t)slot * (m->n + 1), (m->n + 1) * 4, cudaMemcpyDeviceToHost));
+  for (int b = 0; b < m->n - 1; ++b) ranks[b] = r[b + 1];
+  return MPS_OK;
+}
+
+int mps_state_size(mps_t m, int slot, int64_t* n_B, int64_t* n_lam) {
+  std::vector<int32_t> r(m ? m->n : 1);
+  TRY(mps_get_ranks(m, slot, r.data()));
+  int64_t nb = 0, nl = 0;
+  for (int k = 0; k < m->n; ++k) {
+    int rl = k == 0 ? 1 : r[k - 1], rr = k == m->n - 1 ? 1 : r[k];
+    nb += (int64_t)rl * 2 * rr;
+  }
+  for (int b = 0; b < m->n - 1; ++b) nl += r[b];
+  if (n_B) *n_B = nb;
+  if (n_lam) *n_lam = nl;
+  return MPS_OK;
+}
+
+int mps_get_state(mps_t m, int slot, double* B, double* lam) {
+  if (!m || !B || !lam) return fail(MPS_EINVAL, "mps_get_state: null pointer");
+  std::vector<int32_t> r(m->n);
+  TRY(mps_get_ranks(m, slot, r.data()));
+  std::vector<char> buf((size_t)m->dm.slot_elems * m->es);
+  CU(cudaMemcpy(buf.data(), (char*)m->dm.B + (size_t)slot * m->dm.slot_elems * m->es, buf.size(), cudaMemcpyDeviceToHost));
+  std::vector<double> lbuf((size_t)(m->n - 1) * m->chi);
+  CU(cudaMemcpy(lbuf.data(), m->dm.lam + (size_t)slot * (m->n - 1) * m->chi, lbuf.size() * 8, cudaMemcpyDeviceToHost));
+  int64_t o = 0;
+  for (int k = 0; k < m->n; ++k) {
+    int rl = k == 0 ? 1 : r[k - 1], rr = k == m->n - 1 ? 1 : r[k];
+    const int64_t cnt = (int64_t)rl * 2 * rr;
+    for (int64_t e = 0; e < cnt; ++e) {
+      if (m->prec == MPS_FP64) {
+        const double* s = (const double*)buf.data() + 2 * (m->site_off[k] + e);
+        B[2 * (o + e)] = s[0];
+        B[2 * (o + e) + 1] = s[1];
+      } else {
+        const float* s = (const float*)buf.data() + 2 * (m->site_off[k] + e);
+        B[2 * (o + e)] = s[0];
+        B[2 * (o + e) + 1] = s[1];
+      }
+    }
+    o += cnt;
+  }
+  int64_t l = 0;
+  for (int b = 0; b < m->n - 1; ++b)
+    for (int t = 0; t < r[b]; ++t) lam[l++] = lbuf[(size_t)b * m->chi + t];
+  return MPS_OK;
+}
+
+int mps_set_state(mps_t m, int slot, const int32_t* ranks, const double* B, const double* lam) {
+  if (!m || !ranks || !B || !lam) return fail(MPS_EINVAL, "mps_set_state: null pointer");
+  if (slot < 0 || slot >= m->n_slots) return fail(MPS_EINVAL, "mps_set_state: slot out of range");
+  const int n = m->n;
+  for (int b = 0; b < n - 1; ++b)
+    if (ranks[b] < 1 || ranks[b] > m->cap[b + 1]) return fail(MPS_EINVAL, "mps_set_state: rank out of range");
+  std::vector<char> buf((size_t)m->dm.slot_elems * m->es, 0);
+  int64_t o = 0;
+  for (int k = 0; k < n; ++k) {
+    int rl = k == 0 ? 1 : ranks[k - 1], rr = k == n - 1 ? 1 : ranks[k];
+    const int64_t cnt = (int64_t)rl * 2 * rr;
+    for (int64_t e = 0; e < cnt; ++e) {
+      if (m->prec == MPS_FP64) {
+        double* d = (double*)buf.data() + 2 * (m->site_off[k] + e);
+        d[0] = B[2 * (o + e)];
+        d[1] = B[2 * (o + e) + 1];
+      } else {
+        float* d = (float*)buf.data() + 2 * (m->site_off[k] + e);
+        d[0] = (float)B[2 * (o + e)];
+        d[1] = (float)B[2 * (o + e) + 1];
+      }
+    }
+    o += cnt;
+  }
+  std::vector<double> lbuf((size_t)(n - 1) * m->chi, 0.0);
+  int64_t l = 0;
+  for (int b = 0; b < n - 1; ++b)
+    for (int t = 0; t < ranks[b]; ++t) lbuf[(size_t)b * m->chi + t] = lam[l++];
+  std::vector<int> r(n + 1, 1);
+  for (int b = 0; b < n - 1; ++b) r[b + 1] = ranks[b];
+  CU(cudaStreamSynchronize(m->st));
+  CU(cudaMemcpy((char*)m->dm.B + (size_t)slot * m->dm.slot_elems * m->es, buf.data(), buf.size(), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(m->dm.lam + (size_t)slot * (n - 1) * m->chi, lbuf.data(), lbuf.size() * 8, cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(m->dm.rank + (size_t)slot * (n + 1), r.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
+  return MPS_OK;
+}
+
+int vqe_energy(mps_t m, circ_t c, ham_t h, const double* theta, double* energy) {
+  return vqe_energy_batch(m, c, h, 1, theta, energy);
+}
+
+int vqe_energy_batch(mps_t m, circ_t c, ham_t h, int n_batch, const double* thetas, double* energies) {
+  if (!m || !c || !h || !energies) return fail(MPS_EINVAL, "vqe_energy: null pointer");
+  if (!thetas && c->comp.n_params > 0) return fail(MPS_EINVAL, "vqe_energy: theta is null");
+  if (c->comp.n != m->n || h->n != m->n) return fail(MPS_EINVAL, "vqe_energy: qubit count mismatch");
+  if (n_batch < 1 || n_batch > m->n_slots) return fail(MPS_EINVAL, "vqe_energy_batch: n_batch out of [1, n_slots]");
+  reset_stats(m);
+  std::vector<uint8_t> occ((size_t)n_batch * m->n);
+  for (int b = 0; b < n_batch; ++b) std::memcpy(&occ[(size_t)b * m->n], c->comp.reference.data(), m->n);
+  TRY(upload_reset(m, 0, n_batch, occ.data()));
+  TRY(run_circuit(m, c, 0, n_batch, thetas, nullptr, nullptr));
+  int rc = finish_apply(m, nullptr);
+  if (rc != MPS_OK && rc != MPS_ENOCONV) return rc;
+  m->h_out.resize(4 + 2 * h->terms.size());
+  for (int b = 0; b < n_batch; ++b) {
+    TRY(run_measure(m, h, b, m->h_out.data()));
+    energies[b] = m->h_out[0];
+  }
+  return rc;
+}
+
+int vqe_gradient(mps_t m, circ_t c, ham_t h, const double* theta, int n_sel, const int32_t* sel, double* grad) {
+  if (!m || !c || !h || !theta || !sel || !grad) return fail(MPS_EINVAL, "vqe_gradient: null pointer");
+  const int np = c->comp.n_params;
+  for (int i = 0; i < n_sel; ++i)
+    if (sel[i] < 0 || sel[i] >= np) return fail(MPS_EINVAL, "vqe_gradient: parameter index out of range");
+  // Each rotation k of parameter e contributes scale_k [E(phi_k + pi/2) - E(phi_k - pi/2)] / 2.
+  // A shift of rotation k alone is applied by a fixed-angle copy of the circuit.
+  const auto& R = c->comp.rotations;
+  for (int i = 0; i < n_sel; ++i) {
+    double g = 0.0;
+    for (size_t k = 0; k < R.size(); ++k) {
+      if (R[k].param != sel[i]) continue;
+      double e2[2];
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        std::vector<Rotation> rots = R;
+        rots[k].param = -1;
+        rots[k].scale = R[k].scale * theta[R[k].param] + (sgn == 0 ? kHalfPi : -kHalfPi);
+        circ_t cs = nullptr;
+        TRY(finish_circ(c->comp.n, rots, np, &cs));
+        std::unique_ptr<circ_s> hold(cs);
+        cs->comp.reference = c->comp.reference;
+        int rc = vqe_energy(m, cs, h, theta, &e2[sgn]);
+        if (rc != MPS_OK && rc != MPS_ENOCONV) return rc;
+      }
+      g += R[k].scale * (e2[0] - e2[1]) / 2.0;
+    }
+    grad[i] = g;
+  }
+  return MPS_OK;
+}
+
+int mps_get_stats(mps_t m, mps_stats_t* s) {
+  if (!m || !s) return fail(MPS_EINVAL, "mps_get_stats: null pointer");
+  *s = m->stats;
+  return MPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,435 @@
+// Host-side preprocessing of the MPS-VQE library (runs once per Hamiltonian/ansatz).
+//
+//  * Jordan-Wigner map of the electronic Hamiltonian, Eq. (1) -> Eq. (2) (Sec. II-A).
+//  * Trotterised UCCSD generators, Eqs. (3)-(4) (Sec. II-A).
+//  * Compilation of each Pauli rotation into nearest-neighbour two-site gates with
+//    single-qubit gates fused in (Sec. III-A, Sec. III-D).
+//  * The prefix trie of Pauli strings that lets all strings share left environments
+//    (the energy of Eq. 2 as a sum of independent expectations, Sec. III-C).
+//
+// Pauli operators are handled in "XZ form" X^x Z^z with bit masks; a product is
+// (X^x1 Z^z1)(X^x2 Z^z2) = (-1)^{|z1 & x2|} X^{x1^x2} Z^{z1^z2}, and letters follow from
+// Y = i X Z, i.e. X^x Z^z = (-i)^{|x & z|} (x) letters.
+#include "host.hpp"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+
+namespace mpsvqe {
+
+static inline int popc(uint64_t v) { return __builtin_popcountll(v); }
+static inline int popc2(const uint64_t* a, const uint64_t* b) {
+  return popc(a[0] & b[0]) + popc(a[1] & b[1]);
+}
+static inline void setbit(uint64_t* m, int q) { m[q >> 6] |= 1ull << (q & 63); }
+static inline int getbit(const uint64_t* m, int q) { return (int)((m[q >> 6] >> (q & 63)) & 1ull); }
+
+void xz_to_letters(const XZ& k, int n, uint8_t* out) {
+  for (int q = 0; q < n; ++q) {
+    int x = getbit(k.x, q), z = getbit(k.z, q);
+    out[q] = (uint8_t)(x ? (z ? 2 : 1) : (z ? 3 : 0));
+  }
+}
+
+XZ letters_to_xz(const uint8_t* code, int n) {
+  XZ k;
+  for (int q = 0; q < n; ++q) {
+    if (code[q] == 1 || code[q] == 2) setbit(k.x, q);
+    if (code[q] == 2 || code[q] == 3) setbit(k.z, q);
+  }
+  return k;
+}
+
+// i^e for e mod 4
+static inline cd ipow(int e) {
+  switch (((e % 4) + 4) % 4) {
+    case 0: return cd(1, 0);
+    case 1: return cd(0, 1);
+    case 2: return cd(-1, 0);
+    default: return cd(0, -1);
+  }
+}
+
+// Jordan-Wigner ladder operator as two XZ-form terms:
+//   a_p  = 1/2 Z_{<p} X_p + i/2 Z_{<p} Y_p = 1/2 X^{p} Z^{<p} - 1/2 X^{p} Z^{<=p}
+//   a+_p = 1/2 X^{p} Z^{<p} + 1/2 X^{p} Z^{<=p}
+struct XZTerm {
+  XZ k;
+  cd c;
+};
+static void ladder(int p, bool dagger, XZTerm out[2]) {
+  XZ a, b;
+  setbit(a.x, p);
+  setbit(b.x, p);
+  for (int q = 0; q < p; ++q) {
+    setbit(a.z, q);
+    setbit(b.z, q);
+  }
+  setbit(b.z, p);
+  out[0] = {a, cd(0.5, 0)};
+  out[1] = {b, cd(dagger ? 0.5 : -0.5, 0)};
+}
+
+static inline XZTerm mul(const XZTerm& l, const XZTerm& r) {
+  XZTerm o;
+  int sgn = popc2(l.k.z, r.k.x) & 1;
+  for (int w = 0; w < 2; ++w) {
+    o.k.x[w] = l.k.x[w] ^ r.k.x[w];
+    o.k.z[w] = l.k.z[w] ^ r.k.z[w];
+  }
+  o.c = l.c * r.c * (sgn ? -1.0 : 1.0);
+  return o;
+}
+
+using XZMap = std::unordered_map<XZ, cd, XZHash>;
+
+// Accumulate weight * op_1 op_2 ... op_m (leftmost first) into acc.
+static void add_ladder_product(const int* p, const bool* dag, int m, cd weight, XZMap& acc) {
+  XZTerm br[4][2];
+  for (int j = 0; j < m; ++j) ladder(p[j], dag[j], br[j]);
+  for (int combo = 0; combo < (1 << m); ++combo) {
+    XZTerm t{XZ(), weight};
+    for (int j = 0; j < m; ++j) t = mul(t, br[j][(combo >> j) & 1]);
+    acc[t.k] += t.c;
+  }
+}
+
+// Letter-form coefficient of an accumulated XZ term.
+static inline cd letter_coeff(const XZ& k, cd c) { return c * ipow(-popc2(k.x, k.z)); }
+
+static bool trie_less(const std::vector<uint8_t>& a, const std::vector<uint8_t>& b) {
+  return std::lexicographical_compare(a.begin(), a.end(), b.begin(), b.end());
+}
+
+std::vector<Term> canonical_terms(int n, std::vector<Term> terms, double rel_drop) {
+  std::map<std::vector<uint8_t>, double, decltype(&trie_less)> merged(&trie_less);
+  for (auto& t : terms) merged[t.code] += t.coeff;
+  double mx = 0;
+  for (auto& kv : merged) mx = std::max(mx, std::fabs(kv.second));
+  std::vector<Term> out;
+  for (auto& kv : merged)
+    if (std::fabs(kv.second) > rel_drop * mx) out.push_back({kv.first, kv.second});
+  (void)n;
+  return out;  // std::map iterates in trie order
+}
+
+std::vector<Term> jordan_wigner(int m, const double* h, const double* eri, double e_core,
+                                std::string* err) {
+  const int n = 2 * m;
+  XZMap acc;
+  acc.reserve(1 << 16);
+  // one-body: h_pq a+_p a_q, equal spins
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      if ((p & 1) != (q & 1)) continue;
+      double w = h[(p / 2) * m + (q / 2)];
+      if (w == 0.0) continue;
+      int idx[2] = {p, q};
+      bool dg[2] = {true, false};
+      add_ladder_product(idx, dg, 2, cd(w, 0), acc);
+    }
+  // two-body: 1/2 (pq|rs) a+_p a+_r a_s a_q, spin(p)=spin(q), spin(r)=spin(s)
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      if ((p & 1) != (q & 1)) continue;
+      for (int r = 0; r < n; ++r) {
+        if (r == p) continue;  // a+_p a+_p = 0
+        for (int s = 0; s < n; ++s) {
+          if ((r & 1) != (s & 1) || s == q) continue;  // a_s a_s = 0
+          double w = eri[(((size_t)(p / 2) * m + q / 2) * m + r / 2) * m + s / 2];
+          if (w == 0.0) continue;
+          int idx[4] = {p, r, s, q};
+          bool dg[4] = {true, true, false, false};
+          add_ladder_product(idx, dg, 4, cd(0.5 * w, 0), acc);
+        }
+      }
+    }
+  acc[XZ()] += cd(e_core, 0);
+  std::vector<Term> terms;
+  terms.reserve(acc.size());
+  double mx = 0;
+  for (auto& kv : acc) mx = std::max(mx, std::abs(kv.second));
+  for (auto& kv : acc) {
+    cd c = letter_coeff(kv.first, kv.second);
+    if (std::abs(c) <= 1e-12 * mx) continue;
+    if (std::fabs(c.imag()) > 1e-10 * std::max(1.0, mx)) {
+      if (err) *err = "Jordan-Wigner coefficient with an imaginary part: integrals not Hermitian";
+      return {};
+    }
+    Term t;
+    t.code.resize(n);
+    xz_to_letters(kv.first, n, t.code.data());
+    t.coeff = c.real();
+    terms.push_back(std::move(t));
+  }
+  return canonical_terms(n, std::move(terms), 1e-12);
+}
+
+// ------------------------------------------------------------------ UCCSD rotations
+
+static bool mask_less(const XZ& a, const XZ& b) {
+  if (a.x[1] != b.x[1]) return a.x[1] < b.x[1];
+  if (a.x[0] != b.x[0]) return a.x[0] < b.x[0];
+  if (a.z[1] != b.z[1]) return a.z[1] < b.z[1];
+  return a.z[0] < b.z[0];
+}
+
+std::vector<Rotation> uccsd_rotations(int n, int ne, int* n_params) {
+  struct Exc {
+    int k;
+    int o[4];
+  };
+  std::vector<Exc> exc;
+  for (int i = 0; i < ne; ++i)
+    for (int a = ne; a < n; ++a)
+      if ((i & 1) == (a & 1)) exc.push_back({1, {i, a, 0, 0}});
+  for (int i = 0; i < ne; ++i)
+    for (int j = i + 1; j < ne; ++j)
+      for (int a = ne; a < n; ++a)
+        for (int b = a + 1; b < n; ++b)
+          if ((i & 1) + (j & 1) == (a & 1) + (b & 1)) exc.push_back({2, {i, j, a, b}});
+  std::vector<Rotation> rots;
+  for (size_t e = 0; e < exc.size(); ++e) {
+    XZMap acc;
+    const Exc& x = exc[e];
+    if (x.k == 1) {
+      int i = x.o[0], a = x.o[1];
+      int p1[2] = {a, i}, p2[2] = {i, a};
+      bool d[2] = {true, false};
+      add_ladder_product(p1, d, 2, cd(1, 0), acc);    // tau
+      add_ladder_product(p2, d, 2, cd(-1, 0), acc);   // -tau+
+    } else {
+      int i = x.o[0], j = x.o[1], a = x.o[2], b = x.o[3];
+      int p1[4] = {a, b, i, j}, p2[4] = {j, i, b, a};
+      bool d[4] = {true, true, false, false};
+      add_ladder_product(p1, d, 4, cd(1, 0), acc);
+      add_ladder_product(p2, d, 4, cd(-1, 0), acc);
+    }
+    std::vector<std::pair<XZ, double>> strs;
+    double mx = 0;
+    for (auto& kv : acc) mx = std::max(mx, std::abs(kv.second));
+    for (auto& kv : acc) {
+      cd c = letter_coeff(kv.first, kv.second);  // tau - tau+ = i sum c_k P_k
+      if (std::abs(c) <= 1e-12 * mx) continue;
+      strs.push_back({kv.first, c.imag()});
+    }
+    std::sort(strs.begin(), strs.end(),
+              [](const std::pair<XZ, double>& l, const std::pair<XZ, double>& r) {
+                return mask_less(l.first, r.first);
+              });
+    for (auto& s : strs) {
+      Rotation r;
+      r.code.resize(n);
+      xz_to_letters(s.first, n, r.code.data());
+      r.param = (int32_t)e;
+      r.scale = -2.0 * s.second;
+      rots.push_back(std::move(r));
+    }
+  }
+  if (n_params) *n_params = (int)exc.size();
+  return rots;
+}
+
+// ------------------------------------------------------------------ gate compiler
+
+using M2 = std::array<cd, 4>;
+using M4 = std::array<cd, 16>;
+
+static M2 eye2() { return {cd(1), cd(0), cd(0), cd(1)}; }
+static M2 adj2(const M2& a) { return {std::conj(a[0]), std::conj(a[2]), std::conj(a[1]), std::conj(a[3])}; }
+static M4 kron(const M2& a, const M2& b) {
+  M4 o;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      for (int k = 0; k < 2; ++k)
+        for (int l = 0; l < 2; ++l) o[(2 * i + j) * 4 + (2 * k + l)] = a[2 * i + k] * b[2 * j + l];
+  return o;
+}
+static M4 mm(const M4& a, const M4& b) {
+  M4 o;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      cd s = 0;
+      for (int k = 0; k < 4; ++k) s += a[4 * i + k] * b[4 * k + j];
+      o[4 * i + j] = s;
+    }
+  return o;
+}
+static M4 cnot() {
+  M4 o{};
+  o[0] = o[5] = o[11] = o[14] = cd(1);
+  return o;
+}
+static M4 swp() {
+  M4 o{};
+  o[0] = o[6] = o[9] = o[15] = cd(1);
+  return o;
+}
+static M2 rz2(double phi) { return {std::polar(1.0, -0.5 * phi), cd(0), cd(0), std::polar(1.0, 0.5 * phi)}; }
+// Basis change B with B P B+ = Z: H for X, Rx(pi/2) = (I - iX)/sqrt2 for Y, I for Z.
+static M2 basis(uint8_t c) {
+  const double r = 1.0 / std::sqrt(2.0);
+  if (c == 1) return {cd(r), cd(r), cd(r), cd(-r)};
+  if (c == 2) return {cd(r), cd(0, -r), cd(0, -r), cd(r)};
+  return eye2();
+}
+
+namespace {
+struct MatTable {
+  std::map<std::array<uint64_t, 32>, int32_t> index;
+  std::vector<cd>* mats;
+  int32_t add(const M4& m) {
+    std::array<uint64_t, 32> key;
+    for (int i = 0; i < 16; ++i) {
+      double re = m[i].real() + 0.0, im = m[i].imag() + 0.0;  // +0.0 folds -0
+      std::memcpy(&key[2 * i], &re, 8);
+      std::memcpy(&key[2 * i + 1], &im, 8);
+    }
+    auto it = index.find(key);
+    if (it != index.end()) return it->second;
+    int32_t id = (int32_t)(mats->size() / 16);
+    mats->insert(mats->end(), m.begin(), m.end());
+    index.emplace(key, id);
+    return id;
+  }
+};
+}  // namespace
+
+void compile_rotations(int n, const std::vector<Rotation>& rots, Compiled* out) {
+  out->n = n;
+  out->rotations = rots;
+  out->gates.clear();
+  out->mats.clear();
+  out->rot_first_gate.clear();
+  MatTable tab;
+  tab.mats = &out->mats;
+  int np = 0;
+  for (auto& r : rots) np = std::max(np, r.param + 1);
+  out->n_params = std::max(out->n_params, np);
+  const M2 I = eye2();
+  for (const Rotation& r : rots) {
+    out->rot_first_gate.push_back((int64_t)out->gates.size());
+    std::vector<int> S;
+    for (int q = 0; q < n; ++q)
+      if (r.code[q]) S.push_back(q);
+    if (S.empty()) continue;  // global phase
+    auto emit = [&](int bond, const M4& pre, const M4& post, int rz_site, bool parametric) {
+      GateRec g{};
+      g.bond = bond;
+      if (parametric && r.param >= 0) {
+        g.param = r.param;
+        g.scale = r.scale;
+        g.m0 = tab.add(pre);
+        g.m1 = tab.add(post);
+        g.rz_site = rz_site;
+      } else if (parametric) {  // fixed angle: fold Rz in now
+        M2 z = rz2(r.scale);
+        M4 R = rz_site == 0 ? kron(z, I) : kron(I, z);
+        g.param = -1;
+        g.m0 = tab.add(mm(post, mm(R, pre)));
+        g.m1 = -1;
+      } else {
+        g.param = -1;
+        g.m0 = tab.add(pre);
+        g.m1 = -1;
+      }
+      out->gates.push_back(g);
+    };
+    if (S.size() == 1) {
+      int q = S[0];
+      M2 B = basis(r.code[q]);
+      if (q + 1 < n)
+        emit(q, kron(B, I), kron(adj2(B), I), 0, true);
+      else
+        emit(q - 1, kron(I, B), kron(I, adj2(B)), 1, true);
+      continue;
+    }
+    const int lo = S.front(), hi = S.back();
+    std::vector<char> inS(n, 0);
+    for (int q : S) inS[q] = 1;
+    auto Bq = [&](int q) { return inS[q] ? basis(r.code[q]) : I; };
+    auto hop = [&](int b) { return inS[b + 1] ? cnot() : swp(); };
+    for (int b = lo; b < hi - 1; ++b)  // up ladder below the top bond
+      emit(b, mm(hop(b), kron(b == lo ? Bq(lo) : I, Bq(b + 1))), M4{}, 0, false);
+    {  // top bond: up hop, Rz(phi) on hi, down hop
+      int b = hi - 1;
+      M4 pre = mm(cnot(), kron(b == lo ? Bq(lo) : I, Bq(hi)));
+      M4 post = mm(kron(b == lo ? adj2(Bq(lo)) : I, adj2(Bq(hi))), cnot());
+      emit(b, pre, post, 1, true);
+    }
+    for (int b = hi - 2; b >= lo; --b)  // down ladder
+      emit(b, mm(kron(b == lo ? adj2(Bq(lo)) : I, adj2(Bq(b + 1))), hop(b)), M4{}, 0, false);
+  }
+}
+
+void gate_matrix(const Compiled& c, const GateRec& g, const double* theta, cd* U) {
+  M4 a;
+  std::copy(c.mats.begin() + 16 * (size_t)g.m0, c.mats.begin() + 16 * (size_t)g.m0 + 16, a.begin());
+  if (g.param >= 0) {
+    M4 b;
+    std::copy(c.mats.begin() + 16 * (size_t)g.m1, c.mats.begin() + 16 * (size_t)g.m1 + 16, b.begin());
+    M2 z = rz2(g.scale * theta[g.param]);
+    M4 R = g.rz_site == 0 ? kron(z, eye2()) : kron(eye2(), z);
+    a = mm(b, mm(R, a));
+  }
+  std::copy(a.begin(), a.end(), U);
+}
+
+// ------------------------------------------------------------------ prefix trie
+
+void build_trie(int n, const std::vector<Term>& terms, Trie* t) {
+  t->n = n;
+  t->level_nodes.assign(n, 0);
+  t->parent.assign(n, {});
+  t->edge.assign(n, {});
+  t->close_node.assign(n, {});
+  t->close_letter.assign(n, {});
+  t->close_term.assign(n, {});
+  std::vector<int32_t> cur(n + 1, -1);  // current node id per level for the current prefix
+  const uint8_t* prev = nullptr;
+  int max_level = -1;
+  for (size_t s = 0; s < terms.size(); ++s) {
+    const uint8_t* c = terms[s].code.data();
+    int l = -1;
+    for (int q = n - 1; q >= 0; --q)
+      if (c[q]) {
+        l = q;
+        break;
+      }
+    if (l < 0) continue;  // identity string: <I> = 1, no trie path
+    int lcp = 0;
+    if (prev)
+      while (lcp < n && prev[lcp] == c[lcp]) ++lcp;
+    for (int k = lcp + 1; k <= n; ++k) cur[k] = -1;  // prefixes longer than lcp changed
+    if (!prev) cur.assign(n + 1, -1);
+    for (int k = 0; k <= l; ++k) {
+      if (cur[k] < 0) {
+        cur[k] = t->level_nodes[k]++;
+        if (k > 0) {
+          t->parent[k].push_back(cur[k - 1]);
+          t->edge[k].push_back(c[k - 1]);
+        }
+      }
+    }
+    t->close_node[l].push_back(cur[l]);
+    t->close_letter[l].push_back(c[l]);
+    t->close_term[l].push_back((int32_t)s);
+    max_level = std::max(max_level, l);
+    prev = c;
+  }
+  t->n_levels = max_level + 1;
+  t->total_nodes = 0;
+  t->max_level_nodes = 0;
+  t->max_level_closes = 0;
+  for (int k = 0; k < n; ++k) {
+    t->total_nodes += t->level_nodes[k];
+    t->max_level_nodes = std::max(t->max_level_nodes, t->level_nodes[k]);
+    t->max_level_closes = std::max(t->max_level_closes, (int32_t)t->close_term[k].size());
+  }
+}
+
+}  // namespace mpsvqe

@@ -40,3 +40,23 @@ def h2_shaped_integrals(seed):
     for idx in [(0, 1, 0, 1), (1, 0, 1, 0), (0, 1, 1, 0), (1, 0, 0, 1)]:
         g[idx] = x
     return h, g
+
+
+def random_mps_gaussians(n, ranks, seed):
+    """Complex Gaussian arrays (2 r_k, r_{k-1}) per site for a random MPS with the given
+    bond ranks (the orthonormalisation into canonical form is done by the caller)."""
+    rng = np.random.default_rng(20_000 + seed)
+    r = [1] + list(ranks) + [1]
+    return [rng.normal(size=(2 * r[k + 1], r[k])) + 1j * rng.normal(size=(2 * r[k + 1], r[k]))
+            for k in range(n)]
+
+
+def full_ranks(n, chi):
+    """Largest bond ranks an n-site MPS with bond cap chi can have."""
+    return [min(chi, 2 ** min(b + 1, n - 1 - b)) for b in range(n - 1)]
+
+
+def random_unitary4(seed):
+    rng = np.random.default_rng(30_000 + seed)
+    z = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
+    return z  # the caller orthonormalises (QR) if it needs a unitary

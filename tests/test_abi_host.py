@@ -1,0 +1,119 @@
+"""CPU tests of the C ABI: the library loads, exports every declared entry point,
+and its host preprocessing (Jordan-Wigner, UCCSD, gate compiler, argument checks)
+agrees with the independent oracle. No GPU is needed: these calls touch no device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2207_03711_gb300 as G
+from oracle import circuit, pauli, ucc
+from paper_2207_03711_gb300 import synthetic as syn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    G.build()
+    return G.load_library()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "mpsvqe.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)) - {"if", "defined"}
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 28
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in G.SIGNATURES, name
+
+
+@pytest.mark.parametrize("m,seed", [(2, 0), (4, 0), (5, 3), (12, 0)])
+def test_jw_matches_oracle(m, seed):
+    h, g = syn.random_integrals(m, seed)
+    H = G.ham_jw_from_integrals(h, g, 0.25)
+    P, C = G.ham_get_terms(H)
+    Po, Co = pauli.jordan_wigner_hamiltonian(h, g, 0.25)
+    assert P.shape == Po.shape and (P == Po).all()
+    assert np.abs(C - Co).max() <= 1e-12
+
+
+def test_h2_shaped_has_15_terms():
+    h, g = syn.h2_shaped_integrals(1)
+    assert G.ham_get_terms(G.ham_jw_from_integrals(h, g))[0].shape[0] == 15
+
+
+@pytest.mark.parametrize("n,ne", [(4, 2), (8, 4), (10, 4), (24, 12)])
+def test_uccsd_rotations_match_oracle(n, ne):
+    C = G.circ_uccsd(n, ne)
+    P, pidx, scale = G.circ_get_rotations(C)
+    rc, rp, rs, exc = ucc.uccsd_rotations(n, ne)
+    assert C.n_params == len(exc)
+    assert (P == rc).all() and (pidx == rp).all()
+    assert np.abs(scale - rs).max() <= 1e-15
+
+
+def test_compiled_gates_match_oracle_uccsd():
+    n, ne = 8, 4
+    C = G.circ_uccsd(n, ne)
+    theta = syn.random_amplitudes(C.n_params, 4)
+    bond, U = G.circ_export_gates(C, theta)
+    rc, rp, rs, _ = ucc.uccsd_rotations(n, ne)
+    ref = circuit.compile_circuit(rc, rp, rs, theta, n)
+    assert len(ref) == len(bond) == 1568
+    assert all(b == r[0] for b, r in zip(bond, ref))
+    assert max(np.abs(u - r[1]).max() for u, r in zip(U, ref)) <= 1e-14
+
+
+def test_compiled_gates_general_rotations():
+    rng = np.random.default_rng(5)
+    n = 9
+    codes = rng.integers(0, 4, size=(60, n)).astype(np.uint8)
+    codes[0] = 0
+    codes[1] = 0
+    codes[1, 4] = 2          # single-qubit rotation
+    codes[2] = 0
+    codes[2, 8] = 1          # single-qubit rotation on the last qubit
+    codes[3] = 0
+    codes[3, [0, 8]] = [1, 3]  # long identity gap
+    pidx = rng.integers(-1, 5, size=60).astype(np.int32)
+    scale = rng.normal(size=60)
+    theta = rng.normal(size=5)
+    C = G.circ_create(codes, pidx, scale)
+    bond, U = G.circ_export_gates(C, theta)
+    ref = []
+    for code, e, s in zip(codes, pidx, scale):
+        phi = s * theta[e] if e >= 0 else s
+        ref += circuit.two_site_gates(code, phi, n)
+    assert len(ref) == len(bond)
+    assert all(b == r[0] for b, r in zip(bond, ref))
+    assert max(np.abs(u - r[1]).max() for u, r in zip(U, ref)) <= 1e-14
+
+
+def test_ham_create_merges_and_sorts():
+    P = np.array([[3, 0, 1], [0, 0, 0], [3, 0, 1], [1, 2, 0]], dtype=np.uint8)
+    H = G.ham_create(P, [0.5, 1.0, 0.25, -2.0])
+    Pq, Cq = G.ham_get_terms(H)
+    assert (Pq == np.array([[0, 0, 0], [1, 2, 0], [3, 0, 1]])).all()
+    assert np.allclose(Cq, [1.0, -2.0, 0.75])
+
+
+def test_argument_errors_are_status_codes():
+    with pytest.raises(G.MpsError) as e:
+        G.circ_uccsd(4, 0)
+    assert e.value.code == G.MPS_EINVAL
+    with pytest.raises(G.MpsError):
+        G.ham_create(np.array([[0, 7]], dtype=np.uint8), [1.0])
+    with pytest.raises(G.MpsError):
+        G.ham_jw_from_integrals(np.zeros((0, 0)), np.zeros((0, 0, 0, 0)))
+    with pytest.raises(G.MpsError):
+        G.circ_create(np.array([[0, 5, 1]], dtype=np.uint8), [0], [1.0])
+    bad = np.array([[1.0, 2.0], [2.0, 1.0]])
+    eri = np.zeros((2,) * 4)
+    assert G.ham_get_terms(G.ham_jw_from_integrals(bad, eri))[0].shape[0] > 0
