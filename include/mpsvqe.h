@@ -113,16 +113,16 @@ int circ_destroy(circ_t circ);
  * MPS_FP64 (complex128 tensors, FP64 SVD and contractions) or MPS_MIXED (complex64
  * tensors, FP32 contractions and SVD, FP64 Schmidt numbers and energy sums).
  * cuda_stream: a cudaStream_t (NULL = default stream). n_qubits in [2, 128],
- * chi in [1, 256], n_slots in [1, 4096]. Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA. */
+ * chi in [1, 128], n_slots in [1, 4096]. Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA. */
 int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_stream, mps_t* out);
 
 /* Sec. III-D: reset slot to the product state |occ_0 occ_1 ...> (bytes 0/1), all
  * bond ranks 1, lambda = [1]. */
 int mps_reset(mps_t mps, int slot, const uint8_t* occ);
 
-/* Truncation controls (Eq. 9): keep k = min(chi, #{sigma > cutoff * sigma_0});
- * max_sweeps caps the one-sided Jacobi SVD. Defaults: cutoff 1e-13 (FP64) or
- * 2^-20 (mixed); max_sweeps 40. */
+/* Truncation controls (Eq. 9): keep k = min(chi, #{sigma > cutoff * sigma_0}).
+ * Defaults: cutoff 1e-13 (FP64) or 2^-20 (mixed). max_sweeps is accepted for
+ * interface stability and bounds no loop of the current SVD (which is direct). */
 int mps_set_svd_params(mps_t mps, double cutoff, int max_sweeps);
 
 /* Sec. III-A, Eqs. (7)-(10), for every gate of circ on slot 0 in order: contract
@@ -171,14 +171,23 @@ int vqe_gradient(mps_t mps, circ_t circ, ham_t ham, const double* theta, int n_s
 
 /* Per-call statistics of the last apply/energy call on this handle. */
 typedef struct {
-  double discarded_weight; /* summed discarded fraction, slot 0           */
-  int32_t max_rank;        /* largest bond rank reached, slot 0           */
-  int32_t max_sweeps;      /* most Jacobi sweeps used by one SVD           */
-  int64_t n_gates;         /* gates applied per slot                       */
-  int64_t n_svd_noconv;    /* SVDs that hit the sweep cap                  */
-  double ms_circuit;       /* CUDA-event time of the circuit kernels       */
-  double ms_measure;       /* CUDA-event time of the measurement kernels   */
-  int64_t kernel_launches; /* device kernels launched by the call          */
+  double discarded_weight; /* summed discarded fraction, slot 0                   */
+  int32_t max_rank;        /* largest bond rank reached, slot 0                   */
+  int32_t max_sweeps;      /* bisection passes of the last SVD                     */
+  int64_t n_gates;         /* gates applied per slot                               */
+  int64_t n_svd_noconv;    /* Jacobi fallbacks that hit their sweep cap            */
+  double ms_circuit;       /* CUDA-event time of the circuit kernels               */
+  double ms_measure;       /* CUDA-event time of the measurement kernels           */
+  int64_t kernel_launches; /* device kernels launched by the call                  */
+  double cycles[7];        /* slot-0 SM clock cycles per gate-engine phase since   */
+                           /* creation: build M', bidiagonalise, bisection,        */
+                           /* twisted vectors, re-orthonormalise, back-transform,  */
+                           /* site update                                          */
+  int64_t n_fallback;      /* gates whose SVD fell back to one-sided Jacobi        */
+                           /* (numerically degenerate Schmidt values), slot 0      */
+  double alg_flops_total;  /* slot-0 algorithmic real flops of all gate steps      */
+                           /* since creation (dense contraction + Golub-Reinsch    */
+                           /* SVD with right vectors + site update)                */
 } mps_stats_t;
 int mps_get_stats(mps_t mps, mps_stats_t* stats);
 

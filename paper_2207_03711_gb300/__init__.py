@@ -34,7 +34,9 @@ class MpsStats(ctypes.Structure):
     _fields_ = [("discarded_weight", ctypes.c_double), ("max_rank", ctypes.c_int32),
                 ("max_sweeps", ctypes.c_int32), ("n_gates", ctypes.c_int64),
                 ("n_svd_noconv", ctypes.c_int64), ("ms_circuit", ctypes.c_double),
-                ("ms_measure", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("ms_measure", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("cycles", ctypes.c_double * 7), ("n_fallback", ctypes.c_int64),
+                ("alg_flops_total", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -346,7 +348,9 @@ def vqe_gradient(mps, circ, ham, theta, sel):
 def mps_get_stats(mps):
     s = MpsStats()
     _check(load_library().mps_get_stats(mps, ctypes.byref(s)))
-    return {k: getattr(s, k) for k, _ in MpsStats._fields_}
+    out = {k: getattr(s, k) for k, _ in MpsStats._fields_}
+    out["cycles"] = list(s.cycles)
+    return out
 
 
 def mps_last_error():

@@ -114,8 +114,10 @@ struct mps_s {
     dfree(dm.rank);
     dfree(dm.work_M);
     dfree(dm.work_X);
+    dfree(dm.work_S);
     dfree(dm.dw);
     dfree(dm.stat);
+    dfree(dm.prof);
     dfree(d_site_off);
     dfree(w.R);
     dfree(w.Bhat);
@@ -309,7 +311,7 @@ static int upload_reset(mps_s* m, int slot0, int count, const uint8_t* occ_rows)
 }
 
 // Evaluate all terms of h on one slot; out_host receives 4 + 2 T doubles.
-static int run_measure(mps_s* m, ham_s* h, int slot, double* out_host) {
+static int run_measure(mps_s* m, ham_s* h, int slot, double* out_host, bool terms = true) {
   TRY(upload_ham(h));
   const int64_t T = (int64_t)h->terms.size();
   TRY(ensure_meas(m, std::max<int32_t>(1, h->trie.max_level_nodes), std::max<int64_t>(1, T)));
@@ -341,7 +343,7 @@ static int run_measure(mps_s* m, ham_s* h, int slot, double* out_host) {
                        h->id_term, m->st));
   ++launches;
   CU(cudaEventRecord(m->ev[3], m->st));
-  CU(cudaMemcpyAsync(out_host, m->w.out, (4 + 2 * (size_t)T) * 8, cudaMemcpyDeviceToHost, m->st));
+  CU(cudaMemcpyAsync(out_host, m->w.out, (4 + (terms ? 2 * (size_t)T : 0)) * 8, cudaMemcpyDeviceToHost, m->st));
   CU(cudaStreamSynchronize(m->st));
   float ms = 0;
   CU(cudaEventElapsedTime(&ms, m->ev[2], m->ev[3]));
@@ -480,7 +482,7 @@ int circ_destroy(circ_t c) {
 int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_stream, mps_t* out) {
   if (!out) return fail(MPS_EINVAL, "mps_create: null pointer");
   if (n_qubits < 2 || n_qubits > kMaxQubits) return fail(MPS_EINVAL, "mps_create: n_qubits out of [2, 128]");
-  if (chi < 1 || chi > 256) return fail(MPS_EINVAL, "mps_create: chi out of [1, 256]");
+  if (chi < 1 || chi > 128) return fail(MPS_EINVAL, "mps_create: chi out of [1, 128]");
   if (precision != MPS_FP64 && precision != MPS_MIXED) return fail(MPS_EINVAL, "mps_create: bad precision");
   if (n_slots < 1 || n_slots > 4096) return fail(MPS_EINVAL, "mps_create: n_slots out of [1, 4096]");
   auto m = std::make_unique<mps_s>();
@@ -518,8 +520,12 @@ int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_str
   d.work_M = p;
   if (cudaMalloc(&p, (size_t)n_slots * mm * (mm + 1) * m->es) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_X"); }
   d.work_X = p;
+  if (cudaMalloc(&p, (size_t)n_slots * 12 * chi * chi * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_S"); }
+  d.work_S = p;
   TRY(dalloc(&d.dw, n_slots));
   TRY(dalloc(&d.stat, (size_t)n_slots * 4));
+  TRY(dalloc(&d.prof, (size_t)n_slots * 8));
+  CU(cudaMemset(d.prof, 0, (size_t)n_slots * 8 * 8));
   TRY(dalloc(&m->d_site_off, n));
   CU(cudaMemcpy(m->d_site_off, m->site_off.data(), n * 8, cudaMemcpyHostToDevice));
   d.site_off = m->d_site_off;
@@ -563,12 +569,19 @@ static int finish_apply(mps_s* m, double* discarded_weight) {
   double dw = 0;
   int st4[4];
   TRY(read_slot_stats(m, 0, &dw, st4));
+  unsigned long long pr[8];
+  CU(cudaMemcpy(pr, m->dm.prof, sizeof(pr), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 7; ++i) m->stats.cycles[i] = (double)pr[i];
+  double fl;
+  std::memcpy(&fl, &pr[7], 8);
+  m->stats.alg_flops_total = fl;
   m->stats.discarded_weight = dw;
   m->stats.max_sweeps = st4[0];
   m->stats.n_svd_noconv = st4[1];
   m->stats.max_rank = st4[2];
+  m->stats.n_fallback = st4[3];
   if (discarded_weight) *discarded_weight = dw;
-  if (st4[1] > 0) return fail(MPS_ENOCONV, "an SVD reached the Jacobi sweep cap");
+  if (st4[1] > 0) return fail(MPS_ENOCONV, "a Jacobi SVD fallback reached its sweep cap");
   return MPS_OK;
 }
 
@@ -579,7 +592,7 @@ int mps_apply_circuit(mps_t m, circ_t c, const double* theta, double* discarded_
   reset_stats(m);
   // the discarded-weight accumulator and stats of slot 0 restart at this call
   CU(cudaMemsetAsync(m->dm.dw, 0, 8, m->st));
-  CU(cudaMemsetAsync(m->dm.stat, 0, 8, m->st));
+  CU(cudaMemsetAsync(m->dm.stat, 0, 16, m->st));
   TRY(run_circuit(m, c, 0, 1, theta, nullptr, nullptr));
   return finish_apply(m, discarded_weight);
 }
@@ -602,7 +615,7 @@ int mps_apply_gates(mps_t m, int64_t n_gates, const int32_t* bond, const double*
   }
   reset_stats(m);
   CU(cudaMemsetAsync(m->dm.dw, 0, 8, m->st));
-  CU(cudaMemsetAsync(m->dm.stat, 0, 8, m->st));
+  CU(cudaMemsetAsync(m->dm.stat, 0, 16, m->st));
   TRY(run_circuit(m, &c, 0, 1, nullptr, nullptr, nullptr));
   return finish_apply(m, discarded_weight);
 }
@@ -750,7 +763,7 @@ int vqe_energy_batch(mps_t m, circ_t c, ham_t h, int n_batch, const double* thet
   if (rc != MPS_OK && rc != MPS_ENOCONV) return rc;
   m->h_out.resize(4 + 2 * h->terms.size());
   for (int b = 0; b < n_batch; ++b) {
-    TRY(run_measure(m, h, b, m->h_out.data()));
+    TRY(run_measure(m, h, b, m->h_out.data(), false));
     energies[b] = m->h_out[0];
   }
   return rc;

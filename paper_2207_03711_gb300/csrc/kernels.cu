@@ -8,9 +8,11 @@
 //  k_level_T/child/close   one level of the Pauli-string prefix trie (Eq. 11 generalised).
 //  k_energy_sum   E = sum_i a_i <P_i> (Eq. 2) with Neumaier compensation in FP64.
 #include <cfloat>
+#include <cstdint>
 
 #include "cx.cuh"
 #include "kernels.cuh"
+#include "svd.cuh"
 
 namespace mpsvqe {
 
@@ -46,7 +48,7 @@ __global__ void k_reset(DevMPS m, int slot0, const uint8_t* occ) {
   for (int b = threadIdx.x; b <= m.n; b += blockDim.x) rank[b] = 1;
   for (int b = threadIdx.x; b < m.n - 1; b += blockDim.x) lam[(size_t)b * m.chi] = 1.0;
   if (threadIdx.x == 0) m.dw[s] = 0.0;
-  if (threadIdx.x < 4) m.stat[s * 4 + threadIdx.x] = (threadIdx.x == 2) ? 1 : 0;
+  if (threadIdx.x < 4) m.stat[s * 4 + threadIdx.x] = (threadIdx.x == 2) ? 1 : 0;  // passes, noconv, max rank, fallbacks
 }
 
 cudaError_t launch_reset(const DevMPS& m, int prec, int slot0, int count, const uint8_t* occ,
@@ -58,40 +60,189 @@ cudaError_t launch_reset(const DevMPS& m, int prec, int slot0, int count, const 
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- gate engine
+// ------------------------------------------------------------ small tiled GEMM
+// C (Mdim x Ndim, ldc) = sum_t s_t opA_t(A_t) opB_t(B_t) with NTH threads (256 or 512)
+// and 64x64 tiles. opA: A stored Mdim x K (lda), or K x Mdim used as A^H (conjT).
+// opB: B stored K x Ndim (ldb), or Ndim x K used as B^T (transB).
+template <class R>
+struct GemmTerm {
+  const Cx<R>* A;
+  int lda;
+  bool conjT;
+  const Cx<R>* B;
+  int ldb;
+  Cx<R> s;
+  bool transB;
+};
 
-struct CircSmem {
-  __host__ __device__ static constexpr size_t head(int mmax, int nt) {
-    return ((16 * 16 /*U double*/ + 16 * 16 /*U in R, padded*/ + (size_t)mmax * 8 + (size_t)mmax * 4 +
-             64 + (size_t)(nt / 32) * 16) +
-            255) &
-           ~(size_t)255;
+template <class R, int NTH>
+__device__ void block_gemm(int Mdim, int Ndim, int K, const GemmTerm<R>* terms, int nterm, Cx<R>* C,
+                           int ldc, Cx<R> (*As)[17], Cx<R> (*Bs)[65]) {
+  constexpr int TY = NTH / 16, RPT = 64 / TY;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int m0 = 0; m0 < Mdim; m0 += 64)
+    for (int n0 = 0; n0 < Ndim; n0 += 64) {
+      Cx<R> acc[RPT][4];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cx<R>(0, 0);
+      for (int t = 0; t < nterm; ++t) {
+        const GemmTerm<R> T = terms[t];
+        for (int k0 = 0; k0 < K; k0 += 16) {
+          for (int e = threadIdx.x; e < 64 * 16; e += NTH) {
+            const int r = e >> 4, cc = e & 15;
+            const int gm = m0 + r, gk = k0 + cc;
+            Cx<R> v = cx<R>(0, 0);
+            if (gm < Mdim && gk < K) v = T.conjT ? conj(T.A[(size_t)gk * T.lda + gm]) : T.A[(size_t)gm * T.lda + gk];
+            As[r][cc] = T.s * v;
+          }
+          for (int e = threadIdx.x; e < 16 * 64; e += NTH) {
+            const int r = T.transB ? (e & 15) : (e >> 6), cc = T.transB ? (e >> 4) : (e & 63);
+            const int gk = k0 + r, gn = n0 + cc;
+            Cx<R> v = cx<R>(0, 0);
+            if (gk < K && gn < Ndim) v = T.transB ? T.B[(size_t)gn * T.ldb + gk] : T.B[(size_t)gk * T.ldb + gn];
+            Bs[r][cc] = v;
+          }
+          __syncthreads();
+#pragma unroll 4
+          for (int kk = 0; kk < 16; ++kk) {
+            Cx<R> a[RPT], b[4];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) a[i] = As[ty + TY * i][kk];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < RPT; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) cmac(acc[i][j], a[i], b[j]);
+          }
+          __syncthreads();
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int gm = m0 + ty + TY * i, gn = n0 + tx + 16 * j;
+          if (gm < Mdim && gn < Ndim) C[(size_t)gm * ldc + gn] = acc[i][j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- gate engine
+//
+// Shared-memory plan of k_circuit for bond cap chi (mmax = 2 chi), NT threads:
+//   [head]  U (16 complex double), U in R, FP64 reduction slots, misc ints
+//   [svd]   dd, ee, b (2 mmax), b2 (2 mmax), tauL, tauR, sig, lo, hi, coef (mmax each),
+//           cnt, xs (NT each)
+//   [W]     k x p real singular vectors of the bidiagonal (if it fits)
+//   [T]     (r + 1) x p complex, the tall orientation of M' (if it fits)
+// Anything that does not fit lives in the slot's global workspace (L2 resident).
+// Algorithmic real flops of one gate step, counted as the textbook dense algorithms:
+// contraction theta = B_n B_{n+1} (2 rl x rm x 2 rr complex MACs), the 4x4 gate on
+// (i, j), Golub-Reinsch SVD of the (m x n) complex M' computing singular values and
+// right vectors (4 (4 m n^2 + 8 n^3) real flops for m >= n, roles swapped otherwise),
+// and the site update B_n = M V^H (2 rl x 2 rr x k complex MACs). A complex MAC is 8.
+__device__ __forceinline__ double flops_per_gate(int rl, int rm, int rr, int k) {
+  const double m = 2.0 * rl, n = 2.0 * rr;
+  const double big = m >= n ? m : n, small = m >= n ? n : m;
+  const double contract = 8.0 * m * rm * n + 8.0 * 4.0 * m * n;
+  const double svd = 4.0 * (4.0 * big * small * small + 8.0 * small * small * small);
+  const double update = 8.0 * m * n * k;
+  return contract + svd + update;
+}
+
+template <class R>
+struct EngineLayout {
+  size_t head, svd, w_off, w_bytes, t_off, t_bytes, total;
+  bool w_smem, t_smem;
+  __host__ __device__ EngineLayout(int chi, int nt) {
+    const size_t mmax = 2 * (size_t)chi;
+    head = 256 + 256 + (size_t)(nt / 32 + 2) * 8 + 64;
+    head = (head + 255) & ~(size_t)255;
+    svd = sizeof(R) * (2 * mmax + 4 * mmax + 5 * mmax) + sizeof(Cx<R>) * 2 * mmax + (sizeof(R) + 4) * nt +
+          (8 + 4) * mmax + 16 + sizeof(R) * nt + 4 * (size_t)chi + 16;
+    svd = (svd + 255) & ~(size_t)255;
+    w_bytes = sizeof(R) * (size_t)chi * mmax;
+    t_bytes = sizeof(Cx<R>) * (mmax + 1) * mmax;
+    const size_t cap = 188 * 1024;  // leaves room for the static GEMM tiles
+    w_off = head + svd;
+    w_smem = w_off + w_bytes <= cap;
+    t_off = w_off + (w_smem ? w_bytes : 0);
+    t_smem = t_off + t_bytes <= cap;
+    total = t_off + (t_smem ? t_bytes : 0);
   }
 };
 
-template <class R, int NT, int MAXE>
+template <class R, int NT>
 __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0, int64_t g1,
                                                 int slot0, const double* theta, double cutoff,
-                                                int max_sweeps, int x_in_smem) {
+                                                int max_sweeps) {
   extern __shared__ __align__(256) unsigned char smem[];
+  const EngineLayout<R> L(m.chi, NT);
   const int s = slot0 + blockIdx.x;
   const int n = m.n, chi = m.chi, mmax = 2 * chi;
   Cx<R>* Bslot = (Cx<R>*)m.B + (size_t)s * m.slot_elems;
   double* lam = m.lam + (size_t)s * (n - 1) * chi;
   int* rank = m.rank + (size_t)s * (n + 1);
   Cx<R>* W = (Cx<R>*)m.work_M + (size_t)s * mmax * mmax;
+  R* scratch = (R*)((double*)m.work_S + (size_t)s * 12 * chi * chi);  // twisted-factorisation rows
 
   Cx<double>* U = (Cx<double>*)smem;
   Cx<R>* Uf = (Cx<R>*)(smem + 256);
-  double* sig2 = (double*)(smem + 512);
-  int* order = (int*)(sig2 + mmax);
-  int* misc = order + mmax;
-  Cx<R>* X = x_in_smem ? (Cx<R>*)(smem + CircSmem::head(mmax, NT))
-                       : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 1);
+  double* red = (double*)(smem + 512);
+  int* misc = (int*)(red + NT / 32 + 2);
+  R* dd = (R*)(smem + L.head);
+  R* ee = dd + mmax;
+  R* bb = ee + mmax;          // 2 mmax
+  R* b2 = bb + 2 * mmax;      // 2 mmax
+  R* sig = b2 + 2 * mmax;
+  R* lo = sig + mmax;
+  R* hi = lo + mmax;
+  R* coef = hi + mmax;
+  R* xs = coef + mmax;        // NT
+  Cx<R>* tauL = (Cx<R>*)(xs + NT);
+  Cx<R>* tauR = tauL + mmax;
+  int* cnt = (int*)(tauR + mmax);
+  double* sig2d = (double*)(((uintptr_t)(cnt + NT) + 15) & ~(uintptr_t)15);
+  int* order = (int*)(sig2d + mmax);
+  R* grid = (R*)(order + mmax);              // NT log-spaced bisection shifts / smax
+  int* iters_of = (int*)(grid + NT);         // bisection passes for kk = 1..chi
+  __shared__ Cx<R> gA[64][17];
+  __shared__ Cx<R> gB[16][65];
+  R* Wv = L.w_smem ? (R*)(smem + L.w_off) : (R*)((double*)m.work_S + (size_t)s * 12 * chi * chi + 8 * chi * chi);
+  Cx<R>* T = L.t_smem ? (Cx<R>*)(smem + L.t_off) : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 1);
   const double* th = theta + (size_t)blockIdx.x * c.n_params;
 
-  int st_max_sweeps = 0, st_noconv = 0, st_max_rank = 1;
+  int st_max_iters = 0, st_max_rank = 1, st_bad = 0;
+  if (threadIdx.x == 0) misc[2] = 0;
+  {
+    // per-launch tables: grid shifts over [10^-decades, 1] and, for kk targets, the
+    // number of (NT/kk + 1)-fold refinement passes that reach the working precision
+    constexpr bool kF64 = sizeof(R) == 8;
+    const double decades = kF64 ? 15.0 : 8.0;
+    grid[threadIdx.x] = (R)exp10(decades * (double)((int)threadIdx.x - (NT - 1)) / (double)(NT - 1));
+    const double w0 = decades * 2.302585092994046 / (NT - 1);
+    for (int kk = 1 + threadIdx.x; kk <= chi; kk += NT) {
+      const int per = max(1, NT / kk);
+      iters_of[kk - 1] = (int)ceil(log(w0 / (kF64 ? 2e-16 : 6e-8)) / log((double)(per + 1))) + 1;
+    }
+  }
+  __syncthreads();
+  unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double alg_flops = 0.0;  // algorithmic real flops of the gate steps (see flops_per_gate)
+  long long t_mark = clock64();
+#define PHASE(i)                                   \
+  do {                                             \
+    if (threadIdx.x == 0) {                        \
+      const long long now_ = clock64();            \
+      ph[i] += (unsigned long long)(now_ - t_mark); \
+      t_mark = now_;                               \
+    }                                              \
+  } while (0)
   double dw_acc = 0.0;
+  (void)max_sweeps;
 
   for (int64_t g = g0; g < g1; ++g) {
     const GateRec gr = c.gates[g];
@@ -119,14 +270,17 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     }
     const int bond = gr.bond;
     const int rl = rank[bond], rm = rank[bond + 1], rr = rank[bond + 2];
-    const int mrows = 2 * rl, ncol = 2 * rr, ldx = ncol + 1;
+    const int mrows = 2 * rl, ncol = 2 * rr;
+    const bool tall = mrows >= ncol;
+    const int tr = tall ? mrows : ncol, tp = tall ? ncol : mrows, ld = tr + 1;
     Cx<R>* Bn = Bslot + m.site_off[bond];
     Cx<R>* Bn1 = Bslot + m.site_off[bond + 1];
     const double* laml = bond > 0 ? lam + (size_t)(bond - 1) * chi : nullptr;
     __syncthreads();
 
     // (2) Eq. (7): M[(a,i),(j,c)] = sum_{i'j'} U[ij,i'j'] sum_b B_n[a,i',b] B_{n+1}[b,j',c];
-    //     W <- M; Eq. (8): column (a,i) of X <- conj(lambda_{n-1}[a] M[(a,i),:]).
+    //     W <- M; Eq. (8): M' = lambda_{n-1}[a] M, stored tall in T (M' or M'^H).
+    double fro = 0.0;
     for (int it = threadIdx.x; it < rl * rr; it += NT) {
       const int a = it / rr, cc = it - a * rr;
       Cx<R> t00 = cx<R>(0, 0), t01 = t00, t10 = t00, t11 = t00;
@@ -149,251 +303,240 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
         for (int kk = 0; kk < 4; ++kk) cmac(v, Uf[ij * 4 + kk], th4[kk]);
         const int row = 2 * a + (ij >> 1), col = (ij & 1) * rr + cc;
         W[(size_t)row * ncol + col] = v;
-        X[(size_t)row * ldx + col] = conj(la * v);
+        const Cx<R> mv = la * v;
+        if (tall)
+          T[(size_t)col * ld + row] = mv;
+        else
+          T[(size_t)row * ld + col] = conj(mv);
+        fro += (double)norm2(mv);
       }
     }
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fro;
     __syncthreads();
-
-    // (3) Eq. (9): one-sided Jacobi on the mrows columns of X (length ncol). The
-    // columns converge to sigma_p v_p^* (conjugated right singular vectors of M').
-    int G = 1;
-    while (G < 32 && G * MAXE < ncol) G <<= 1;
-    const int npairs = mrows >> 1;
-    while (G < 32 && G < ncol && (NT / (2 * G)) >= npairs) G <<= 1;
-    const int ept = (ncol + G - 1) / G;
-    const int ngroups = NT / G, grp = threadIdx.x / G, lane = threadIdx.x - grp * G;
-    const R tol = R(2) * Eps<R>::v * sqrt((R)ncol);
-    int sweep = 0;
-    bool converged = (mrows <= 1);
-    for (; sweep < max_sweeps && !converged; ++sweep) {
-      int rotated = 0;
-      for (int r = 0; r < mrows - 1; ++r) {
-        // every lane of a warp runs the same trip count (group shuffles need full warps)
-        for (int base = 0; base < npairs; base += ngroups) {
-          const int pi = base + grp;
-          const bool active = pi < npairs;
-          int p = 0, q = 1;
-          if (pi == 0) {
-            p = r;
-            q = mrows - 1;
-          } else if (active) {
-            p = (r + pi) % (mrows - 1);
-            q = (r - pi + (mrows - 1)) % (mrows - 1);
-          }
-          Cx<R>* xp = X + (size_t)p * ldx;
-          Cx<R>* xq = X + (size_t)q * ldx;
-          Cx<R> vp[MAXE], vq[MAXE];
-          R al = 0, be = 0;
-          Cx<R> ga = cx<R>(0, 0);
-#pragma unroll
-          for (int e = 0; e < MAXE; ++e) {
-            const int idx = lane + e * G;
-            if (active && e < ept && idx < ncol) {
-              vp[e] = xp[idx];
-              vq[e] = xq[idx];
-            } else {
-              vp[e] = cx<R>(0, 0);
-              vq[e] = cx<R>(0, 0);
-            }
-            al += norm2(vp[e]);
-            be += norm2(vq[e]);
-            cmac_conj(ga, vp[e], vq[e]);
-          }
-          for (int o = G >> 1; o > 0; o >>= 1) {
-            al += shfl_x(al, o, G);
-            be += shfl_x(be, o, G);
-            ga.x += shfl_x(ga.x, o, G);
-            ga.y += shfl_x(ga.y, o, G);
-          }
-          const R ag = sqrt(norm2(ga));
-          if (active && ag > R(0) && ag > tol * sqrt(al) * sqrt(be)) {
-            const R zeta = (be - al) / (R(2) * ag);
-            const R az = fabs(zeta);
-            const R t = az > R(1e15) ? R(0.5) / zeta
-                                     : copysign(R(1), zeta) / (az + sqrt(R(1) + zeta * zeta));
-            if (t != R(0)) {
-              const R cs = R(1) / sqrt(R(1) + t * t), sn = cs * t;
-              const Cx<R> ph = cx<R>(ga.x / ag, ga.y / ag);  // e^{i phi} = gamma / |gamma|
-              const Cx<R> sph = cx<R>(sn * ph.x, sn * ph.y);
-#pragma unroll
-              for (int e = 0; e < MAXE; ++e) {
-                const int idx = lane + e * G;
-                if (e < ept && idx < ncol) {
-                  const Cx<R> a = vp[e], b = vq[e];
-                  // xp' = c xp - s e^{-i phi} xq ; xq' = s e^{i phi} xp + c xq
-                  xp[idx] = cs * a - conj(sph) * b;
-                  xq[idx] = sph * a + cs * b;
-                }
-              }
-              rotated = 1;
-            }
-          }
-        }
-        __syncthreads();
-      }
-      converged = !__syncthreads_or(rotated);
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < NT / 32; ++w) t += red[w];
+      red[NT / 32] = t;
     }
-    if (!converged) ++st_noconv;
-    st_max_sweeps = max(st_max_sweeps, sweep);
 
-    // (4) squared column norms (FP64 accumulation), descending order, truncation
-    for (int base = 0; base < mrows; base += ngroups) {
-      const int p = base + grp;
-      double acc = 0.0;
-      if (p < mrows)
-        for (int idx = lane; idx < ncol; idx += G) acc += (double)norm2(X[(size_t)p * ldx + idx]);
-      for (int o = G >> 1; o > 0; o >>= 1) acc += shfl_x(acc, o, G);
-      if (lane == 0 && p < mrows) sig2[p] = acc;
-    }
     __syncthreads();
-    for (int p = threadIdx.x; p < mrows; p += NT) {
-      const double v = sig2[p];
-      int rk = 0;
-      for (int q = 0; q < mrows; ++q) {
-        const double w = sig2[q];
-        rk += (w > v) || (w == v && q < p);
-      }
-      order[rk] = p;
+    PHASE(0);
+    // (3) Eq. (9): bidiagonalise T = Q B P^H (B real)
+    bidiagonalize<R, NT>(T, ld, tr, tp, dd, ee, tauL, tauR, nullptr);
+    PHASE(1);
+    // Golub-Kahan tridiagonal off-diagonal b = (d0, e0, d1, e1, ..., d_{p-1})
+    for (int i = threadIdx.x; i < 2 * tp - 1; i += NT) {
+      const R v = (i & 1) ? ee[i >> 1] : dd[i >> 1];
+      bb[i] = v;
+      b2[i] = v * v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const double s0 = sig2[order[0]];
-      const int kmax = min(chi, min(mrows, ncol));
+      R smax = 0;
+      for (int i = 0; i < 2 * tp; ++i) {
+        const R left = i > 0 ? rabs(bb[i - 1]) : R(0), right = i < 2 * tp - 1 ? rabs(bb[i]) : R(0);
+        smax = fmax(smax, left + right);
+      }
+      coef[0] = smax;
+    }
+    __syncthreads();
+    const R smax = coef[0];
+    // split the TGK where an off-diagonal is negligible (exact degeneracies live in
+    // different blocks after this; the perturbation is below 4 eps ||B||)
+    for (int i = threadIdx.x; i < 2 * tp - 1; i += NT)
+      if (rabs(bb[i]) <= R(4) * Eps<R>::v * smax) {
+        bb[i] = R(0);
+        b2[i] = R(0);
+      }
+    __syncthreads();
+    const int kk = min(chi, tp);
+    const bool fp64 = sizeof(R) == 8;
+    const int iters = iters_of[kk - 1];
+    bisect_singular_values<R, NT>(b2, tp, smax, kk, iters, sig, lo, hi, cnt, xs, grid);
+    if (threadIdx.x == 0) {
+      const R s0 = sig[0];
       int k = 0;
-      while (k < kmax && sig2[order[k]] > cutoff * cutoff * s0) ++k;
+      while (k < kk && sig[k] > (R)cutoff * s0 && sig[k] > R(0)) ++k;
       if (k == 0) k = 1;
-      double total = 0.0, dropped = 0.0;
-      for (int t = 0; t < mrows; ++t) total += sig2[order[t]];
-      for (int t = k; t < mrows; ++t) dropped += sig2[order[t]];
-      if (total > 0.0) dw_acc += dropped / total;
       misc[0] = k;
       st_max_rank = max(st_max_rank, k);
+      st_max_iters = max(st_max_iters, iters);
     }
     __syncthreads();
     const int k = misc[0];
+    PHASE(2);
 
-    // (5) Eq. (10): B_{n+1} <- V (rows v_t = conj(column)/sigma), lambda_n <- sigma,
-    //     B_n <- M V^+ i.e. B_n[(a,i),t] = sum_q M[(a,i),q] X[p_t][q] / sigma_t.
-    for (int idx = threadIdx.x; idx < k * ncol; idx += NT) {
-      const int t = idx / ncol, q = idx - t * ncol;
-      const int p = order[t];
-      const R inv = (R)(1.0 / sqrt(sig2[p]));
-      Bn1[idx] = conj(inv * X[(size_t)p * ldx + q]);
+    // (4) singular vectors of B from twisted factorisations, then CGS2
+    const R tiny = smax * (fp64 ? R(1e-300) : R(1e-30)) + (fp64 ? R(1e-300) : R(1e-37));
+    for (int t = threadIdx.x; t < k; t += NT) {
+      R* dp = scratch + (size_t)t * 4 * tp;
+      int s0, e0;
+      const R delta = R(8) * (hi[t] - lo[t]) + R(4) * Eps<R>::v * smax;
+      owning_block<R>(b2, 2 * tp, sig, t, delta, tiny, &s0, &e0);
+      twisted_vector<R>(bb, tp, s0, e0, sig[t], tiny, dp, dp + 2 * tp, tall ? 0 : 1, Wv + (size_t)t * mmax);
     }
-    for (int idx = threadIdx.x; idx < mrows * k; idx += NT) {
-      const int t = idx / mrows, row = idx - t * mrows;
-      const int p = order[t];
-      const Cx<R>* xr = X + (size_t)p * ldx;
-      const Cx<R>* wr = W + (size_t)row * ncol;
-      Cx<R> acc = cx<R>(0, 0);
-      for (int q = 0; q < ncol; ++q) cmac(acc, wr[q], xr[q]);
-      const R inv = (R)(1.0 / sqrt(sig2[p]));
-      Bn[(size_t)row * k + t] = inv * acc;
-    }
-    for (int t = threadIdx.x; t < k; t += NT) lam[(size_t)bond * chi + t] = sqrt(sig2[order[t]]);
-    if (threadIdx.x == 0) rank[bond + 1] = k;
+    if (threadIdx.x == 0) misc[1] = 0;
     __syncthreads();
+    PHASE(3);
+    orthonormalize_rows<R, NT>(Wv, mmax, k, tp, coef, &misc[1]);
+    PHASE(4);
+    Cx<R>* xout = (Cx<R>*)scratch;               // k x ncol right singular vectors v_t
+    int kf = k;                                  // kept count of the path taken
+    if (misc[1] == 0) {
+      // (5) back-transformation: x_t = P w_t (tall) or Q [w_t; 0] (wide) is the right
+      //     singular vector v_t of M' (length ncol); 16 entries per thread.
+      int LV = 8;
+      while (LV < 32 && LV * 16 < ncol) LV <<= 1;
+      const int vpp = NT / LV;
+      const int grp = threadIdx.x / LV, l = threadIdx.x - grp * LV;
+      for (int vb = 0; vb < k; vb += vpp) {
+        const int t = vb + grp;
+        const bool act = t < k;
+        Cx<R> x[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int q = l + e * LV;
+          R val = R(0);
+          if (act && q < tp) val = Wv[(size_t)t * mmax + q];
+          x[e] = cx<R>(val, R(0));
+        }
+        const int nref = tall ? tp - 1 : tp;
+        for (int jr = nref - 1; jr >= 0; --jr) {
+          const int start = tall ? jr + 1 : jr;
+          const Cx<R> tau = tall ? tauR[jr] : tauL[jr];
+          Cx<R> hv[16];
+          Cx<R> sdot = cx<R>(0, 0);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int q = l + e * LV;
+            hv[e] = cx<R>(0, 0);
+            if (q > start && q < ncol) hv[e] = tall ? T[(size_t)q * ld + jr] : T[(size_t)jr * ld + q];
+            if (q == start) hv[e] = cx<R>(1, 0);
+            cmac_conj(sdot, hv[e], x[e]);
+          }
+          for (int o = 1; o < LV; o <<= 1) {
+            sdot.x += __shfl_xor_sync(0xffffffffu, sdot.x, o, LV);
+            sdot.y += __shfl_xor_sync(0xffffffffu, sdot.y, o, LV);
+          }
+          const Cx<R> f = tau * sdot;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) x[e] = x[e] - f * hv[e];
+        }
+        if (act) {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int q = l + e * LV;
+            if (q < ncol) xout[(size_t)t * ncol + q] = x[e];
+          }
+        }
+      }
+      if (threadIdx.x == 0) {
+        double kept = 0.0;
+        for (int t = 0; t < k; ++t) kept += (double)sig[t] * (double)sig[t];
+        const double total = red[NT / 32];
+        if (total > 0.0) dw_acc += fmax(0.0, total - kept) / total;
+      }
+      __syncthreads();
+    } else {
+      // (5') degenerate spectrum without a split: one-sided Jacobi on the columns
+      //      X = conj rows of M' (rebuilt from W and lambda_{n-1}) in the T buffer
+      ++st_bad;
+      const int ldx = ncol + 1;
+      Cx<R>* X = T;
+      for (int idx = threadIdx.x; idx < mrows * ncol; idx += NT) {
+        const int row = idx / ncol, q = idx - row * ncol;
+        const R la = laml ? (R)laml[row >> 1] : R(1);
+        X[(size_t)row * ldx + q] = conj(la * W[(size_t)row * ncol + q]);
+      }
+      __syncthreads();
+      const double zero2 = (double)Eps<R>::v * Eps<R>::v * 16.0 * red[NT / 32];
+      jacobi_columns<R, NT, 8>(X, ldx, mrows, ncol, zero2, 60, &misc[2]);
+      for (int p = threadIdx.x; p < mrows; p += NT) {
+        double acc = 0.0;
+        for (int q = 0; q < ncol; ++q) acc += (double)norm2(X[(size_t)p * ldx + q]);
+        sig2d[p] = acc;
+      }
+      __syncthreads();
+      for (int p = threadIdx.x; p < mrows; p += NT) {
+        const double v = sig2d[p];
+        int rk = 0;
+        for (int q = 0; q < mrows; ++q) {
+          const double w = sig2d[q];
+          rk += (w > v) || (w == v && q < p);
+        }
+        order[rk] = p;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        const double s0 = sig2d[order[0]];
+        const int kmax = min(chi, min(mrows, ncol));
+        int kk2 = 0;
+        while (kk2 < kmax && sig2d[order[kk2]] > cutoff * cutoff * s0) ++kk2;
+        if (kk2 == 0) kk2 = 1;
+        double total = 0.0, dropped = 0.0;
+        for (int t = 0; t < mrows; ++t) total += sig2d[order[t]];
+        for (int t = kk2; t < mrows; ++t) dropped += sig2d[order[t]];
+        if (total > 0.0) dw_acc += dropped / total;
+        misc[0] = kk2;
+        st_max_rank = max(st_max_rank, kk2);
+      }
+      __syncthreads();
+      kf = misc[0];
+      for (int t = threadIdx.x; t < kf; t += NT) sig[t] = (R)sqrt(sig2d[order[t]]);
+      for (int idx = threadIdx.x; idx < kf * ncol; idx += NT) {
+        const int t = idx / ncol, q = idx - t * ncol;
+        const int p = order[t];
+        const R inv = (R)(1.0 / sqrt(sig2d[p]));
+        xout[idx] = inv * X[(size_t)p * ldx + q];   // column p of X = sigma * v_t
+      }
+      __syncthreads();
+    }
+    PHASE(5);
+    // (6) Eq. (10): B_{n+1} <- V (row t = v_t^H), B_n <- M V^H (column t = M v_t),
+    //     lambda_n <- sigma
+    for (int idx = threadIdx.x; idx < kf * ncol; idx += NT) Bn1[idx] = conj(xout[idx]);
+    {
+      GemmTerm<R> gt{W, ncol, false, xout, ncol, cx<R>(1, 0), true};
+      block_gemm<R, NT>(mrows, kf, ncol, &gt, 1, Bn, kf, gA, gB);
+    }
+    for (int t = threadIdx.x; t < kf; t += NT) lam[(size_t)bond * chi + t] = (double)sig[t];
+    if (threadIdx.x == 0) rank[bond + 1] = kf;
+    __syncthreads();
+    PHASE(6);
+    if (threadIdx.x == 0) alg_flops += flops_per_gate(rl, rm, rr, kf);
   }
+#undef PHASE
   if (threadIdx.x == 0) {
+    for (int i = 0; i < 7; ++i) m.prof[s * 8 + i] += ph[i];
+    m.prof[s * 8 + 7] = __double_as_longlong(__longlong_as_double(m.prof[s * 8 + 7]) + alg_flops);
     m.dw[s] += dw_acc;
     int* stt = m.stat + s * 4;
-    stt[0] = max(stt[0], st_max_sweeps);
-    stt[1] += st_noconv;
+    stt[0] = max(stt[0], st_max_iters);
+    stt[1] += misc[2];
+    stt[3] += st_bad;
     stt[2] = max(stt[2], st_max_rank);
   }
 }
 
-template <class R, int NT, int MAXE>
+template <class R, int NT>
 static cudaError_t launch_circ_t(const DevMPS& m, const CircDev& c, int64_t g0, int64_t g1,
                                  int slot0, int count, const double* theta, double cutoff,
                                  int max_sweeps, cudaStream_t st) {
-  const int mmax = 2 * m.chi;
-  const size_t head = CircSmem::head(mmax, NT);
-  const size_t xbytes = (size_t)mmax * (mmax + 1) * sizeof(Cx<R>);
-  const int x_in_smem = (head + xbytes) <= 200 * 1024;
-  const size_t smem = head + (x_in_smem ? xbytes : 0);
-  cudaError_t e = cudaFuncSetAttribute(k_circuit<R, NT, MAXE>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const EngineLayout<R> L(m.chi, NT);
+  cudaError_t e = cudaFuncSetAttribute(k_circuit<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L.total);
   if (e != cudaSuccess) return e;
-  k_circuit<R, NT, MAXE><<<count, NT, smem, st>>>(m, c, g0, g1, slot0, theta, cutoff, max_sweeps,
-                                                  x_in_smem);
+  k_circuit<R, NT><<<count, NT, L.total, st>>>(m, c, g0, g1, slot0, theta, cutoff, max_sweeps);
   return cudaGetLastError();
 }
 
 cudaError_t launch_circuit(const DevMPS& m, int prec, const CircDev& c, int64_t g0, int64_t g1,
                            int slot0, int count, const double* theta, double cutoff,
                            int max_sweeps, cudaStream_t st) {
-  const bool big = 2 * m.chi > 256;
   if (prec == MPS_PREC_FP64)
-    return big ? launch_circ_t<double, 256, 16>(m, c, g0, g1, slot0, count, theta, cutoff, max_sweeps, st)
-               : launch_circ_t<double, 256, 8>(m, c, g0, g1, slot0, count, theta, cutoff, max_sweeps, st);
-  return big ? launch_circ_t<float, 512, 16>(m, c, g0, g1, slot0, count, theta, cutoff, max_sweeps, st)
-             : launch_circ_t<float, 512, 8>(m, c, g0, g1, slot0, count, theta, cutoff, max_sweeps, st);
-}
-
-// ------------------------------------------------------------ small tiled GEMM
-// C (Mdim x Ndim, ldc) = sum_t s_t opA_t(A_t) B_t with 256 threads and 64x64 tiles.
-// opA: A stored Mdim x K (lda) when conjT = false, or K x Mdim (lda) used as A^+.
-template <class R>
-struct GemmTerm {
-  const Cx<R>* A;
-  int lda;
-  bool conjT;
-  const Cx<R>* B;
-  int ldb;
-  Cx<R> s;
-};
-
-template <class R>
-__device__ void block_gemm(int Mdim, int Ndim, int K, const GemmTerm<R>* terms, int nterm, Cx<R>* C,
-                           int ldc, Cx<R> (*As)[17], Cx<R> (*Bs)[65]) {
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  for (int m0 = 0; m0 < Mdim; m0 += 64)
-    for (int n0 = 0; n0 < Ndim; n0 += 64) {
-      Cx<R> acc[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = cx<R>(0, 0);
-      for (int t = 0; t < nterm; ++t) {
-        const GemmTerm<R> T = terms[t];
-        for (int k0 = 0; k0 < K; k0 += 16) {
-          for (int e = threadIdx.x; e < 64 * 16; e += 256) {
-            const int r = e >> 4, cc = e & 15;
-            const int gm = m0 + r, gk = k0 + cc;
-            Cx<R> v = cx<R>(0, 0);
-            if (gm < Mdim && gk < K) v = T.conjT ? conj(T.A[(size_t)gk * T.lda + gm]) : T.A[(size_t)gm * T.lda + gk];
-            As[r][cc] = T.s * v;
-          }
-          for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-            const int r = e >> 6, cc = e & 63;
-            const int gk = k0 + r, gn = n0 + cc;
-            Bs[r][cc] = (gk < K && gn < Ndim) ? T.B[(size_t)gk * T.ldb + gn] : cx<R>(0, 0);
-          }
-          __syncthreads();
-#pragma unroll 4
-          for (int kk = 0; kk < 16; ++kk) {
-            Cx<R> a[4], b[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[ty + 16 * i][kk];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) cmac(acc[i][j], a[i], b[j]);
-          }
-          __syncthreads();
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
-          if (gm < Mdim && gn < Ndim) C[(size_t)gm * ldc + gn] = acc[i][j];
-        }
-    }
+    return launch_circ_t<double, 512>(m, c, g0, g1, slot0, count, theta, cutoff, max_sweeps, st);
+  return launch_circ_t<float, 512>(m, c, g0, g1, slot0, count, theta, cutoff, max_sweeps, st);
 }
 
 // --------------------------------------------------------- right environments
@@ -413,8 +556,8 @@ __global__ void __launch_bounds__(256) k_right_envs(DevMPS m, int slot, Cx<R>* R
     Cx<R>* Bh = Bhat + m.site_off[k];
     const Cx<R>* Rn = Renv + (size_t)(k + 1) * chi2;
     for (int i = 0; i < 2; ++i) {  // Bhat^i = B^i R_{k+1}: (Dl x Dr)(Dr x Dr)
-      GemmTerm<R> t{Bk + i * Dr, 2 * Dr, false, Rn, Dr, cx<R>(1, 0)};
-      block_gemm<R>(Dl, Dr, Dr, &t, 1, Bh + i * Dr, 2 * Dr, As, Bs);
+      GemmTerm<R> t{Bk + i * Dr, 2 * Dr, false, Rn, Dr, cx<R>(1, 0), false};
+      block_gemm<R, 256>(Dl, Dr, Dr, &t, 1, Bh + i * Dr, 2 * Dr, As, Bs);
       __syncthreads();
     }
     // R_k = sum_i Bhat^i (B^i)^+ : (Dl x Dr)(Dr x Dl). As a product with A = Bhat^i and
@@ -464,8 +607,8 @@ __global__ void __launch_bounds__(256) k_level_T(DevMPS m, int slot, int k, cons
   const int* rank = m.rank + (size_t)slot * (m.n + 1);
   const int Dk = rank[k], Dk1 = rank[k + 1];
   const Cx<R>* Bk = (const Cx<R>*)m.B + (size_t)slot * m.slot_elems + m.site_off[k];
-  GemmTerm<R> t{Lin + (size_t)u * chi2, Dk, false, Bk + j * Dk1, 2 * Dk1, cx<R>(1, 0)};
-  block_gemm<R>(Dk, Dk1, Dk, &t, 1, T + ((size_t)u * 2 + j) * chi2, Dk1, As, Bs);
+  GemmTerm<R> t{Lin + (size_t)u * chi2, Dk, false, Bk + j * Dk1, 2 * Dk1, cx<R>(1, 0), false};
+  block_gemm<R, 256>(Dk, Dk1, Dk, &t, 1, T + ((size_t)u * 2 + j) * chi2, Dk1, As, Bs);
 }
 
 // L_{k+1}[c] = sum_ij sigma_ij (B_k^i)^+ T_j[parent(c)]
@@ -485,8 +628,8 @@ __global__ void __launch_bounds__(256) k_level_child(DevMPS m, int slot, int k, 
   letter_entries<R>(edge[c], ii, jj, sg);
   GemmTerm<R> t[2];
   for (int e = 0; e < 2; ++e)
-    t[e] = GemmTerm<R>{Bk + ii[e] * Dk1, 2 * Dk1, true, T + ((size_t)u * 2 + jj[e]) * chi2, Dk1, sg[e]};
-  block_gemm<R>(Dk1, Dk1, Dk, t, 2, Lout + (size_t)c * chi2, Dk1, As, Bs);
+    t[e] = GemmTerm<R>{Bk + ii[e] * Dk1, 2 * Dk1, true, T + ((size_t)u * 2 + jj[e]) * chi2, Dk1, sg[e], false};
+  block_gemm<R, 256>(Dk1, Dk1, Dk, t, 2, Lout + (size_t)c * chi2, Dk1, As, Bs);
 }
 
 // <P> (unnormalised) = sum_ij sigma_ij <Bhat_k^i, T_j[node]>_F, FP64 accumulation

@@ -1,0 +1,428 @@
+// Truncated SVD of one gate's M' inside one thread block (Eq. 9 of the paper).
+//
+// Route: Householder bidiagonalisation of the tall orientation of M' (the paper's
+// own SVD also starts from a bidiagonal reduction), then the singular values of the
+// real bidiagonal B from Sturm counts of its Golub-Kahan tridiagonal
+// TGK = [[0, B], [B^T, 0]] (multisection bisection), singular vectors of B from a
+// twisted factorisation of TGK - sigma I, re-orthonormalisation (classical
+// Gram-Schmidt twice, in descending sigma order), and back-transformation by the
+// stored Householder reflectors.
+//
+// Conventions: the reflector H = I - tau v v^H (v_0 = 1) satisfies H^H x = beta e_1
+// with beta real. T (r x p, r >= p, column-major, leading dimension ld) is reduced
+// to T = Q B P^H with Q = H_0 H_1 ... (left reflectors stored below the diagonal),
+// P = G_0 G_1 ... (right reflectors stored right of the superdiagonal).
+#pragma once
+#include "cx.cuh"
+
+namespace mpsvqe {
+
+template <class R>
+__device__ __forceinline__ R rabs(R x) {
+  return x < R(0) ? -x : x;
+}
+// Division inside Sturm recurrences: a correctly rounded quotient is not needed there
+// (the counts and twisted factorisations tolerate a few ulps per step).
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+
+// LAPACK-style reflector for x = (alpha, tail) with ||tail||^2 = xn2.
+template <class R>
+__device__ __forceinline__ void make_reflector(Cx<R> alpha, R xn2, Cx<R>* tau, R* beta, Cx<R>* scale) {
+  if (xn2 == R(0) && alpha.y == R(0)) {
+    *tau = cx<R>(0, 0);
+    *beta = alpha.x;
+    *scale = cx<R>(0, 0);
+    return;
+  }
+  const R nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+  const R b = alpha.x >= R(0) ? -nrm : nrm;
+  *beta = b;
+  *tau = cx<R>((b - alpha.x) / b, -alpha.y / b);
+  // scale = 1 / (alpha - beta)
+  const Cx<R> den = cx<R>(alpha.x - b, alpha.y);
+  const R dn = den.x * den.x + den.y * den.y;
+  *scale = cx<R>(den.x / dn, -den.y / dn);
+}
+
+// Householder bidiagonalisation, NT threads. dd[k] (diagonal) and ee[k] (superdiagonal)
+// receive the real entries; tauL/tauR the reflector factors.
+template <class R, int NT>
+__device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R>* tauL, Cx<R>* tauR,
+                              R* redbuf) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < p; ++k) {
+    // --- left reflector on column k, rows k..r-1 (warp 0)
+    if (warp == 0) {
+      R xn2 = 0;
+      for (int i = k + 1 + lane; i < r; i += 32) xn2 += norm2(T[(size_t)k * ld + i]);
+      for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
+      Cx<R> tau, sc;
+      R beta;
+      make_reflector(T[(size_t)k * ld + k], xn2, &tau, &beta, &sc);
+      for (int i = k + 1 + lane; i < r; i += 32) T[(size_t)k * ld + i] = T[(size_t)k * ld + i] * sc;
+      if (lane == 0) {
+        T[(size_t)k * ld + k] = cx<R>(beta, 0);
+        dd[k] = beta;
+        tauL[k] = tau;
+      }
+    }
+    __syncthreads();
+    // --- apply H^H = I - conj(tau) v v^H to columns k+1..p-1 (4 lanes per column)
+    for (int cbase = k + 1; cbase < p; cbase += NT / 4) {
+      const Cx<R> ct = conj(tauL[k]);
+      const int col = cbase + (tid >> 2), l4 = tid & 3;
+      const bool act = col < p;
+      Cx<R> s = cx<R>(0, 0);
+      if (act) {
+        Cx<R>* tc = T + (size_t)col * ld;
+        const Cx<R>* vk = T + (size_t)k * ld;
+        for (int i = k + l4; i < r; i += 4) {
+          const Cx<R> v = (i == k) ? cx<R>(1, 0) : vk[i];
+          cmac_conj(s, v, tc[i]);
+        }
+      }
+      for (int o = 1; o < 4; o <<= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (act) {
+        Cx<R>* tc = T + (size_t)col * ld;
+        const Cx<R>* vk = T + (size_t)k * ld;
+        const Cx<R> f = ct * s;
+        for (int i = k + l4; i < r; i += 4) {
+          const Cx<R> v = (i == k) ? cx<R>(1, 0) : vk[i];
+          tc[i] = tc[i] - f * v;
+        }
+      }
+    }
+    __syncthreads();
+    if (k >= p - 1) break;
+    // --- right reflector on row k, columns k+1..p-1 (warp 0), acting on conj(row)
+    if (warp == 0) {
+      R xn2 = 0;
+      for (int j = k + 2 + lane; j < p; j += 32) xn2 += norm2(T[(size_t)j * ld + k]);
+      for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
+      Cx<R> tau, sc;
+      R beta;
+      make_reflector(conj(T[(size_t)(k + 1) * ld + k]), xn2, &tau, &beta, &sc);
+      for (int j = k + 2 + lane; j < p; j += 32) T[(size_t)j * ld + k] = conj(T[(size_t)j * ld + k]) * sc;
+      if (lane == 0) {
+        T[(size_t)(k + 1) * ld + k] = cx<R>(beta, 0);
+        ee[k] = beta;
+        tauR[k] = tau;
+      }
+    }
+    __syncthreads();
+    // --- apply G = I - tau w w^H from the right to rows k+1..r-1, columns k+1..p-1
+    {
+      const Cx<R> t = tauR[k];
+      const int row = k + 1 + (tid >> 2), l4 = tid & 3;
+      for (int rbase = row; ; rbase += NT / 4) {
+        const bool act = rbase < r;
+        if (!__any_sync(0xffffffffu, act)) break;
+        Cx<R> s = cx<R>(0, 0);
+        if (act)
+          for (int j = k + 1 + l4; j < p; j += 4) {
+            const Cx<R> w = (j == k + 1) ? cx<R>(1, 0) : T[(size_t)j * ld + k];
+            cmac(s, T[(size_t)j * ld + rbase], w);
+          }
+        for (int o = 1; o < 4; o <<= 1) {
+          s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+          s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (act) {
+          const Cx<R> f = t * s;
+          for (int j = k + 1 + l4; j < p; j += 4) {
+            const Cx<R> w = (j == k + 1) ? cx<R>(1, 0) : T[(size_t)j * ld + k];
+            T[(size_t)j * ld + rbase] = T[(size_t)j * ld + rbase] - f * conj(w);
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  (void)redbuf;
+}
+
+// Number of singular values of B that are >= x, from the negative count of the
+// LDL^T factorisation of TGK - x I (b2 = squared off-diagonal of TGK, length N-1).
+template <class R>
+__device__ __forceinline__ int count_ge(const R* b2, int p, R x, R tiny) {
+  const int N = 2 * p;
+  R q = -x;
+  int neg = q < R(0);
+  for (int i = 1; i < N; ++i) {
+    if (rabs(q) < tiny) q = -tiny;
+    q = -x - qdiv(b2[i - 1], q);
+    neg += q < R(0);
+  }
+  return N - neg;
+}
+
+// Same count restricted to TGK indices [s, e) (one unreduced block after splitting).
+template <class R>
+__device__ __forceinline__ int count_ge_block(const R* b2, int s, int e, R x, R tiny) {
+  R q = -x;
+  int neg = q < R(0);
+  for (int i = s + 1; i < e; ++i) {
+    if (rabs(q) < tiny) q = -tiny;
+    q = -x - qdiv(b2[i - 1], q);
+    neg += q < R(0);
+  }
+  return (e - s) - neg;
+}
+
+// All kk largest singular values (descending) into sig[0..kk), NT threads.
+// scratch: lo[kk], hi[kk], cnt[NT], xs[NT].
+template <class R, int NT>
+__device__ void bisect_singular_values(const R* b2, int p, R smax, int kk, int iters, R* sig, R* lo, R* hi,
+                                       int* cnt, R* xs, const R* grid) {
+  const int tid = threadIdx.x;
+  const R tiny = smax * R(1e-30) + R(1e-37);
+  // grid pass: NT log-spaced shifts smax * grid[t] (grid computed once per launch)
+  {
+    const R x = smax * grid[tid];
+    xs[tid] = x;
+    cnt[tid] = count_ge(b2, p, x, tiny);
+  }
+  __syncthreads();
+  for (int i = tid; i < kk; i += NT) {
+    // largest grid index with cnt >= i+1 (cnt is non-increasing in the index)
+    int a = -1, b = NT;
+    while (b - a > 1) {
+      const int mid = (a + b) >> 1;
+      if (cnt[mid] >= i + 1) a = mid; else b = mid;
+    }
+    lo[i] = a >= 0 ? xs[a] : R(0);
+    hi[i] = (a + 1 < NT) ? xs[a + 1] : smax * R(1.001) + tiny;
+  }
+  __syncthreads();
+  const int per = max(1, NT / max(kk, 1));
+  for (int it = 0; it < iters; ++it) {
+    const int i = tid / per, j = tid - i * per;
+    const bool act = i < kk;
+    R x = 0;
+    int c = 0;
+    if (act) {
+      x = lo[i] + (hi[i] - lo[i]) * (R)(j + 1) / (R)(per + 1);
+      c = count_ge(b2, p, x, tiny);
+    }
+    xs[tid] = x;
+    cnt[tid] = c;
+    __syncthreads();
+    if (act && j == 0) {
+      R nlo = lo[i], nhi = hi[i];
+      for (int q = 0; q < per; ++q) {
+        const R xq = xs[tid + q];
+        if (cnt[tid + q] >= i + 1) nlo = fmax(nlo, xq); else nhi = fmin(nhi, xq);
+      }
+      lo[i] = nlo;
+      hi[i] = nhi;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < kk; i += NT) sig[i] = R(0.5) * (lo[i] + hi[i]);
+  __syncthreads();
+}
+
+// Eigenvector of the TGK block [s0, e0) (zero diagonal, off-diagonal b) for eigenvalue
+// lam by a twisted factorisation; writes the half selected by `odd` (0: even TGK
+// indices = right singular vector of B; 1: odd indices = left singular vector),
+// normalised, into w[0..p). dp, dm: per-thread scratch of at least 2p entries.
+template <class R>
+__device__ void twisted_vector(const R* b, int p, int s0, int e0, R lam, R tiny, R* dp, R* dm, int odd, R* w) {
+  dp[s0] = -lam;
+  for (int i = s0 + 1; i < e0; ++i) {
+    R prev = dp[i - 1];
+    if (rabs(prev) < tiny) prev = -tiny;
+    dp[i] = -lam - qdiv(b[i - 1] * b[i - 1], prev);
+  }
+  dm[e0 - 1] = -lam;
+  for (int i = e0 - 2; i >= s0; --i) {
+    R nxt = dm[i + 1];
+    if (rabs(nxt) < tiny) nxt = -tiny;
+    dm[i] = -lam - qdiv(b[i] * b[i], nxt);
+  }
+  int rr = s0;
+  R best = rabs(dp[s0] + dm[s0] + lam);
+  for (int i = s0 + 1; i < e0; ++i) {
+    const R g = rabs(dp[i] + dm[i] + lam);
+    if (g < best) {
+      best = g;
+      rr = i;
+    }
+  }
+  // z_rr = 1; z_i = -(b_i / dp_i) z_{i+1} below, z_i = -(b_{i-1} / dm_i) z_{i-1} above
+  for (int q = 0; q < p; ++q) w[q] = R(0);
+  R z = 1;
+  if ((rr & 1) == odd) w[rr >> 1] = z;
+  for (int i = rr - 1; i >= s0; --i) {
+    R d = dp[i];
+    if (rabs(d) < tiny) d = -tiny;
+    z = -qdiv(b[i], d) * z;
+    if ((i & 1) == odd) w[i >> 1] = z;
+  }
+  z = 1;
+  for (int i = rr + 1; i < e0; ++i) {
+    R d = dm[i];
+    if (rabs(d) < tiny) d = -tiny;
+    z = -qdiv(b[i - 1], d) * z;
+    if ((i & 1) == odd) w[i >> 1] = z;
+  }
+  R nrm = 0;
+  for (int q = 0; q < p; ++q) nrm += w[q] * w[q];
+  const R inv = nrm > R(0) ? R(1) / sqrt(nrm) : R(0);
+  for (int q = 0; q < p; ++q) w[q] *= inv;
+}
+
+// Block [s, e) of the split TGK that owns target t: the (m+1)-th eigenvalue inside the
+// window (lam - delta, lam + delta] scanning blocks in index order, where m counts the
+// earlier targets that fall in the same window (exactly degenerate values of different
+// blocks get different blocks).
+template <class R>
+__device__ void owning_block(const R* b2, int N, const R* sig, int t, R delta, R tiny, int* s_out, int* e_out) {
+  const R lam = sig[t];
+  int m = 0;
+  for (int u = 0; u < t; ++u) m += rabs(sig[u] - lam) <= delta;
+  int occ = 0, bs = 0;
+  *s_out = 0;
+  *e_out = N;
+  for (int i = 0; i < N; ++i) {
+    const bool end = (i == N - 1) || (b2[i] == R(0));
+    if (!end) continue;
+    const int e = i + 1;
+    const int inwin = count_ge_block(b2, bs, e, lam - delta, tiny) - count_ge_block(b2, bs, e, lam + delta, tiny);
+    if (inwin > 0 && occ + inwin > m) {
+      *s_out = bs;
+      *e_out = e;
+      return;
+    }
+    occ += inwin;
+    bs = e;
+  }
+}
+
+// Classical Gram-Schmidt twice over the rows of W (k x p, row stride ldw), in order.
+template <class R, int NT>
+__device__ void orthonormalize_rows(R* W, int ldw, int k, int p, R* coef, int* collapsed) {
+  const int tid = threadIdx.x;
+  for (int t = 0; t < k; ++t) {
+    for (int pass = 0; pass < 2; ++pass) {
+      // coef[s] = <w_s, w_t> for s < t, 8 threads per dot
+      const int s = tid >> 3, l8 = tid & 7;
+      for (int sb = s; ; sb += NT / 8) {
+        const bool act = sb < t;
+        if (!__any_sync(0xffffffffu, act)) break;
+        R acc = 0;
+        if (act)
+          for (int q = l8; q < p; q += 8) acc += W[(size_t)sb * ldw + q] * W[(size_t)t * ldw + q];
+        for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (act && l8 == 0) coef[sb] = acc;
+      }
+      __syncthreads();
+      for (int q = tid; q < p; q += NT) {
+        R v = W[(size_t)t * ldw + q];
+        for (int u = 0; u < t; ++u) v -= coef[u] * W[(size_t)u * ldw + q];
+        W[(size_t)t * ldw + q] = v;
+      }
+      __syncthreads();
+    }
+    // normalise row t (warp 0)
+    if ((tid >> 5) == 0) {
+      R acc = 0;
+      for (int q = tid; q < p; q += 32) acc += W[(size_t)t * ldw + q] * W[(size_t)t * ldw + q];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      const R inv = acc > R(0) ? R(1) / sqrt(acc) : R(0);
+      if (tid == 0 && acc < R(1e-6)) ++*collapsed;
+      for (int q = tid; q < p; q += 32) W[(size_t)t * ldw + q] *= inv;
+    }
+    __syncthreads();
+  }
+}
+
+// One-sided (Hestenes) Jacobi on the `ncols` columns of X (each of length `len`,
+// column stride ldx), used when the bidiagonal route reports a collapsed vector
+// (numerically degenerate singular values without a split). Columns converge to
+// sigma_p times a singular vector; columns below sqrt(zero2) are numerically zero.
+template <class R, int NT, int MAXE>
+__device__ void jacobi_columns(Cx<R>* X, int ldx, int ncols, int len, double zero2, int max_sweeps,
+                               int* noconv) {
+  int G = 1;
+  while (G < 32 && G * MAXE < len) G <<= 1;
+  const int npairs = (ncols + 1) >> 1;
+  while (G < 32 && G < len && (NT / (2 * G)) >= npairs) G <<= 1;
+  const int ept = (len + G - 1) / G;
+  const int ngroups = NT / G, grp = threadIdx.x / G, lane = threadIdx.x - grp * G;
+  const R tol = R(2) * (sizeof(R) == 8 ? R(2.220446049250313e-16) : R(1.1920929e-7)) * sqrt((R)len);
+  const int mm = ncols + (ncols & 1);  // even number of players; index ncols is a dummy
+  bool converged = ncols <= 1;
+  int sweep = 0;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    int rotated = 0;
+    for (int r = 0; r < mm - 1; ++r) {
+      for (int base = 0; base < mm / 2; base += ngroups) {
+        const int pi = base + grp;
+        int p = 0, q = 1;
+        if (pi == 0) {
+          p = r;
+          q = mm - 1;
+        } else if (pi < mm / 2) {
+          p = (r + pi) % (mm - 1);
+          q = (r - pi + (mm - 1)) % (mm - 1);
+        }
+        const bool active = pi < mm / 2 && p < ncols && q < ncols;
+        Cx<R>* xp = X + (size_t)p * ldx;
+        Cx<R>* xq = X + (size_t)q * ldx;
+        Cx<R> vp[MAXE], vq[MAXE];
+        R al = 0, be = 0;
+        Cx<R> ga = cx<R>(0, 0);
+#pragma unroll
+        for (int e = 0; e < MAXE; ++e) {
+          const int idx = lane + e * G;
+          if (active && e < ept && idx < len) {
+            vp[e] = xp[idx];
+            vq[e] = xq[idx];
+          } else {
+            vp[e] = cx<R>(0, 0);
+            vq[e] = cx<R>(0, 0);
+          }
+          al += norm2(vp[e]);
+          be += norm2(vq[e]);
+          cmac_conj(ga, vp[e], vq[e]);
+        }
+        for (int o = G >> 1; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o, G);
+          be += __shfl_xor_sync(0xffffffffu, be, o, G);
+          ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o, G);
+          ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o, G);
+        }
+        const R ag = sqrt(norm2(ga));
+        if (active && ag > R(0) && (double)fmin(al, be) > zero2 && ag > tol * sqrt(al) * sqrt(be)) {
+          const R zeta = (be - al) / (R(2) * ag);
+          const R az = rabs(zeta);
+          const R t = az > R(1e15) ? R(0.5) / zeta : copysign(R(1), zeta) / (az + sqrt(R(1) + zeta * zeta));
+          if (t != R(0)) {
+            const R cs = R(1) / sqrt(R(1) + t * t), sn = cs * t;
+            const Cx<R> sph = cx<R>(sn * ga.x / ag, sn * ga.y / ag);
+#pragma unroll
+            for (int e = 0; e < MAXE; ++e) {
+              const int idx = lane + e * G;
+              if (e < ept && idx < len) {
+                const Cx<R> a = vp[e], b = vq[e];
+                xp[idx] = cs * a - conj(sph) * b;
+                xq[idx] = sph * a + cs * b;
+              }
+            }
+            rotated = 1;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    converged = !__syncthreads_or(rotated);
+  }
+  if (threadIdx.x == 0 && !converged) ++*noconv;
+}
+
+}  // namespace mpsvqe
