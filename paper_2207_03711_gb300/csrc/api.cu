@@ -520,7 +520,7 @@ int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_str
   d.work_M = p;
   if (cudaMalloc(&p, (size_t)n_slots * mm * (mm + 1) * m->es) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_X"); }
   d.work_X = p;
-  if (cudaMalloc(&p, (size_t)n_slots * 12 * chi * chi * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_S"); }
+  if (cudaMalloc(&p, (size_t)n_slots * 16 * chi * chi * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_S"); }
   d.work_S = p;
   TRY(dalloc(&d.dw, n_slots));
   TRY(dalloc(&d.stat, (size_t)n_slots * 4));

@@ -164,9 +164,10 @@ struct EngineLayout {
     svd = sizeof(R) * (2 * mmax + 4 * mmax + 5 * mmax) + sizeof(Cx<R>) * 2 * mmax + (sizeof(R) + 4) * nt +
           (8 + 4) * mmax + 16 + sizeof(R) * nt + 4 * (size_t)chi + 16;
     svd = (svd + 255) & ~(size_t)255;
-    w_bytes = sizeof(R) * (size_t)chi * mmax;
+    w_bytes = sizeof(R) * ((size_t)chi * (mmax + 1) + (size_t)chi * chi);   // W rows + Gram
     t_bytes = sizeof(Cx<R>) * (mmax + 1) * mmax;
-    const size_t cap = 188 * 1024;  // leaves room for the static GEMM tiles
+    // the static site-update GEMM tiles (64x17 + 16x65 complex) share the 227 KB
+    const size_t cap = 226 * 1024 - sizeof(Cx<R>) * (64 * 17 + 16 * 65) - 512;
     w_off = head + svd;
     w_smem = w_off + w_bytes <= cap;
     t_off = w_off + (w_smem ? w_bytes : 0);
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   double* lam = m.lam + (size_t)s * (n - 1) * chi;
   int* rank = m.rank + (size_t)s * (n + 1);
   Cx<R>* W = (Cx<R>*)m.work_M + (size_t)s * mmax * mmax;
-  R* scratch = (R*)((double*)m.work_S + (size_t)s * 12 * chi * chi);  // twisted-factorisation rows
+  R* scratch = (R*)((double*)m.work_S + (size_t)s * 16 * chi * chi);  // twisted-factorisation rows
 
   Cx<double>* U = (Cx<double>*)smem;
   Cx<R>* Uf = (Cx<R>*)(smem + 256);
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   int* iters_of = (int*)(grid + NT);         // bisection passes for kk = 1..chi
   __shared__ Cx<R> gA[64][17];
   __shared__ Cx<R> gB[16][65];
-  R* Wv = L.w_smem ? (R*)(smem + L.w_off) : (R*)((double*)m.work_S + (size_t)s * 12 * chi * chi + 8 * chi * chi);
+  R* Wv = L.w_smem ? (R*)(smem + L.w_off) : (R*)((double*)m.work_S + (size_t)s * 16 * chi * chi + 8 * chi * chi);
   Cx<R>* T = L.t_smem ? (Cx<R>*)(smem + L.t_off) : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 1);
   const double* th = theta + (size_t)blockIdx.x * c.n_params;
 
@@ -322,8 +323,9 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
 
     __syncthreads();
     PHASE(0);
-    // (3) Eq. (9): bidiagonalise T = Q B P^H (B real)
-    bidiagonalize<R, NT>(T, ld, tr, tp, dd, ee, tauL, tauR, nullptr);
+    // (3) Eq. (9): bidiagonalise T = Q B P^H (B real); the reflector vectors are staged
+    //     in the (not yet used) singular-vector buffer
+    bidiagonalize<R, NT>(T, ld, tr, tp, dd, ee, tauL, tauR, (Cx<R>*)Wv, (Cx<R>*)Wv + mmax);
     PHASE(1);
     // Golub-Kahan tridiagonal off-diagonal b = (d0, e0, d1, e1, ..., d_{p-1})
     for (int i = threadIdx.x; i < 2 * tp - 1; i += NT) {
@@ -370,16 +372,18 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     // (4) singular vectors of B from twisted factorisations, then CGS2
     const R tiny = smax * (fp64 ? R(1e-300) : R(1e-30)) + (fp64 ? R(1e-300) : R(1e-37));
     for (int t = threadIdx.x; t < k; t += NT) {
-      R* dp = scratch + (size_t)t * 4 * tp;
+      // scratch rows interleaved over the k threads: dp at [i k + t], dm after 2p k entries
+      R* dp = scratch + t;
       int s0, e0;
       const R delta = R(8) * (hi[t] - lo[t]) + R(4) * Eps<R>::v * smax;
       owning_block<R>(b2, 2 * tp, sig, t, delta, tiny, &s0, &e0);
-      twisted_vector<R>(bb, tp, s0, e0, sig[t], tiny, dp, dp + 2 * tp, tall ? 0 : 1, Wv + (size_t)t * mmax);
+      twisted_vector<R>(bb, tp, s0, e0, sig[t], tiny, dp, dp + (size_t)2 * tp * k, k, tall ? 0 : 1,
+                        Wv + (size_t)t * (mmax + 1));
     }
     if (threadIdx.x == 0) misc[1] = 0;
     __syncthreads();
     PHASE(3);
-    orthonormalize_rows<R, NT>(Wv, mmax, k, tp, coef, &misc[1]);
+    orthonormalize_rows_chol<R, NT>(Wv, mmax + 1, k, tp, Wv + (size_t)chi * (mmax + 1), &misc[1]);
     PHASE(4);
     Cx<R>* xout = (Cx<R>*)scratch;               // k x ncol right singular vectors v_t
     int kf = k;                                  // kept count of the path taken
@@ -398,7 +402,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
         for (int e = 0; e < 16; ++e) {
           const int q = l + e * LV;
           R val = R(0);
-          if (act && q < tp) val = Wv[(size_t)t * mmax + q];
+          if (act && q < tp) val = Wv[(size_t)t * (mmax + 1) + q];
           x[e] = cx<R>(val, R(0));
         }
         const int nref = tall ? tp - 1 : tp;

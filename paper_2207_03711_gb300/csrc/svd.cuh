@@ -45,12 +45,20 @@ __device__ __forceinline__ void make_reflector(Cx<R> alpha, R xn2, Cx<R>* tau, R
   *scale = cx<R>(den.x / dn, -den.y / dn);
 }
 
-// Householder bidiagonalisation, NT threads. dd[k] (diagonal) and ee[k] (superdiagonal)
-// receive the real entries; tauL/tauR the reflector factors.
+// Householder bidiagonalisation, NT threads, T in shared (or global) memory. dd[k]
+// (diagonal) and ee[k] (superdiagonal) receive the real entries; tauL/tauR the
+// reflector factors. Each column (left update) or row (right update) is handled by 8
+// lanes that keep their 16 entries in registers between the dot product and the
+// rank-1 update, so every element is read and written once per half step.
+// vb, wb: shared scratch of >= r and >= p complex entries (reflector vectors).
 template <class R, int NT>
 __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R>* tauL, Cx<R>* tauR,
-                              R* redbuf) {
+                              Cx<R>* vb, Cx<R>* wb) {
+  constexpr int EPL = sizeof(R) == 4 ? 16 : 8;   // entries per lane
+  int LPC = 8;                                     // lanes per column / row
+  while (LPC < 32 && LPC * EPL < (r > p ? r : p)) LPC <<= 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = tid / LPC, l8 = tid % LPC;
   for (int k = 0; k < p; ++k) {
     // --- left reflector on column k, rows k..r-1 (warp 0)
     if (warp == 0) {
@@ -60,39 +68,50 @@ __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R
       Cx<R> tau, sc;
       R beta;
       make_reflector(T[(size_t)k * ld + k], xn2, &tau, &beta, &sc);
-      for (int i = k + 1 + lane; i < r; i += 32) T[(size_t)k * ld + i] = T[(size_t)k * ld + i] * sc;
+      for (int i = k + 1 + lane; i < r; i += 32) {
+        const Cx<R> v = T[(size_t)k * ld + i] * sc;
+        T[(size_t)k * ld + i] = v;
+        vb[i] = v;
+      }
       if (lane == 0) {
         T[(size_t)k * ld + k] = cx<R>(beta, 0);
+        vb[k] = cx<R>(1, 0);
         dd[k] = beta;
         tauL[k] = tau;
       }
     }
     __syncthreads();
-    // --- apply H^H = I - conj(tau) v v^H to columns k+1..p-1 (4 lanes per column)
-    for (int cbase = k + 1; cbase < p; cbase += NT / 4) {
+    // --- apply H^H = I - conj(tau) v v^H to columns k+1..p-1
+    {
       const Cx<R> ct = conj(tauL[k]);
-      const int col = cbase + (tid >> 2), l4 = tid & 3;
-      const bool act = col < p;
-      Cx<R> s = cx<R>(0, 0);
-      if (act) {
-        Cx<R>* tc = T + (size_t)col * ld;
-        const Cx<R>* vk = T + (size_t)k * ld;
-        for (int i = k + l4; i < r; i += 4) {
-          const Cx<R> v = (i == k) ? cx<R>(1, 0) : vk[i];
-          cmac_conj(s, v, tc[i]);
+      const int nr = r - k;
+      Cx<R> v[EPL];
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const int i = k + l8 + LPC * e;
+        v[e] = (l8 + LPC * e < nr) ? vb[i] : cx<R>(0, 0);
+      }
+      for (int cbase = k + 1; cbase < p; cbase += NT / LPC) {
+        const int col = cbase + grp;
+        const bool act = col < p;
+        Cx<R>* tc = T + (size_t)(act ? col : k) * ld;
+        Cx<R> x[EPL];
+        Cx<R> s = cx<R>(0, 0);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int off = l8 + LPC * e;
+          x[e] = (act && off < nr) ? tc[k + off] : cx<R>(0, 0);
+          cmac_conj(s, v[e], x[e]);
         }
-      }
-      for (int o = 1; o < 4; o <<= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-      }
-      if (act) {
-        Cx<R>* tc = T + (size_t)col * ld;
-        const Cx<R>* vk = T + (size_t)k * ld;
+        for (int o = 1; o < LPC; o <<= 1) {
+          s.x += __shfl_xor_sync(0xffffffffu, s.x, o, LPC);
+          s.y += __shfl_xor_sync(0xffffffffu, s.y, o, LPC);
+        }
         const Cx<R> f = ct * s;
-        for (int i = k + l4; i < r; i += 4) {
-          const Cx<R> v = (i == k) ? cx<R>(1, 0) : vk[i];
-          tc[i] = tc[i] - f * v;
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int off = l8 + LPC * e;
+          if (act && off < nr) tc[k + off] = x[e] - f * v[e];
         }
       }
     }
@@ -106,9 +125,14 @@ __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R
       Cx<R> tau, sc;
       R beta;
       make_reflector(conj(T[(size_t)(k + 1) * ld + k]), xn2, &tau, &beta, &sc);
-      for (int j = k + 2 + lane; j < p; j += 32) T[(size_t)j * ld + k] = conj(T[(size_t)j * ld + k]) * sc;
+      for (int j = k + 2 + lane; j < p; j += 32) {
+        const Cx<R> w = conj(T[(size_t)j * ld + k]) * sc;
+        T[(size_t)j * ld + k] = w;
+        wb[j] = w;
+      }
       if (lane == 0) {
         T[(size_t)(k + 1) * ld + k] = cx<R>(beta, 0);
+        wb[k + 1] = cx<R>(1, 0);
         ee[k] = beta;
         tauR[k] = tau;
       }
@@ -117,32 +141,39 @@ __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R
     // --- apply G = I - tau w w^H from the right to rows k+1..r-1, columns k+1..p-1
     {
       const Cx<R> t = tauR[k];
-      const int row = k + 1 + (tid >> 2), l4 = tid & 3;
-      for (int rbase = row; ; rbase += NT / 4) {
-        const bool act = rbase < r;
-        if (!__any_sync(0xffffffffu, act)) break;
+      const int nc = p - k - 1;
+      Cx<R> w[EPL];
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const int off = l8 + LPC * e;
+        w[e] = (off < nc) ? wb[k + 1 + off] : cx<R>(0, 0);
+      }
+      for (int rbase = k + 1; rbase < r; rbase += NT / LPC) {
+        const int row = rbase + grp;
+        const bool act = row < r;
+        const int rr = act ? row : k;
+        Cx<R> x[EPL];
         Cx<R> s = cx<R>(0, 0);
-        if (act)
-          for (int j = k + 1 + l4; j < p; j += 4) {
-            const Cx<R> w = (j == k + 1) ? cx<R>(1, 0) : T[(size_t)j * ld + k];
-            cmac(s, T[(size_t)j * ld + rbase], w);
-          }
-        for (int o = 1; o < 4; o <<= 1) {
-          s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-          s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int off = l8 + LPC * e;
+          x[e] = (act && off < nc) ? T[(size_t)(k + 1 + off) * ld + rr] : cx<R>(0, 0);
+          cmac(s, x[e], w[e]);
         }
-        if (act) {
-          const Cx<R> f = t * s;
-          for (int j = k + 1 + l4; j < p; j += 4) {
-            const Cx<R> w = (j == k + 1) ? cx<R>(1, 0) : T[(size_t)j * ld + k];
-            T[(size_t)j * ld + rbase] = T[(size_t)j * ld + rbase] - f * conj(w);
-          }
+        for (int o = 1; o < LPC; o <<= 1) {
+          s.x += __shfl_xor_sync(0xffffffffu, s.x, o, LPC);
+          s.y += __shfl_xor_sync(0xffffffffu, s.y, o, LPC);
+        }
+        const Cx<R> f = t * s;
+#pragma unroll
+        for (int e = 0; e < EPL; ++e) {
+          const int off = l8 + LPC * e;
+          if (act && off < nc) T[(size_t)(k + 1 + off) * ld + rr] = x[e] - f * conj(w[e]);
         }
       }
     }
     __syncthreads();
   }
-  (void)redbuf;
 }
 
 // Number of singular values of B that are >= x, from the negative count of the
@@ -152,6 +183,7 @@ __device__ __forceinline__ int count_ge(const R* b2, int p, R x, R tiny) {
   const int N = 2 * p;
   R q = -x;
   int neg = q < R(0);
+#pragma unroll 8
   for (int i = 1; i < N; ++i) {
     if (rabs(q) < tiny) q = -tiny;
     q = -x - qdiv(b2[i - 1], q);
@@ -165,6 +197,7 @@ template <class R>
 __device__ __forceinline__ int count_ge_block(const R* b2, int s, int e, R x, R tiny) {
   R q = -x;
   int neg = q < R(0);
+#pragma unroll 4
   for (int i = s + 1; i < e; ++i) {
     if (rabs(q) < tiny) q = -tiny;
     q = -x - qdiv(b2[i - 1], q);
@@ -231,23 +264,28 @@ __device__ void bisect_singular_values(const R* b2, int p, R smax, int kk, int i
 // indices = right singular vector of B; 1: odd indices = left singular vector),
 // normalised, into w[0..p). dp, dm: per-thread scratch of at least 2p entries.
 template <class R>
-__device__ void twisted_vector(const R* b, int p, int s0, int e0, R lam, R tiny, R* dp, R* dm, int odd, R* w) {
-  dp[s0] = -lam;
+__device__ void twisted_vector(const R* b, int p, int s0, int e0, R lam, R tiny, R* dp, R* dm, int stride, int odd,
+                               R* w) {
+  // dp, dm: this thread's scratch, entry i at [i * stride] (threads interleaved, so a
+  // group of threads stepping through i touches consecutive addresses)
+  dp[(size_t)s0 * stride] = -lam;
+  R prev = -lam;
   for (int i = s0 + 1; i < e0; ++i) {
-    R prev = dp[i - 1];
     if (rabs(prev) < tiny) prev = -tiny;
-    dp[i] = -lam - qdiv(b[i - 1] * b[i - 1], prev);
+    prev = -lam - qdiv(b[i - 1] * b[i - 1], prev);
+    dp[(size_t)i * stride] = prev;
   }
-  dm[e0 - 1] = -lam;
+  // backward pass fused with the twist search: gamma_i = dp_i + dm_i + lam
+  int rr = e0 - 1;
+  R nxt = -lam;
+  dm[(size_t)(e0 - 1) * stride] = nxt;
+  R best = rabs(dp[(size_t)(e0 - 1) * stride] + nxt + lam);
   for (int i = e0 - 2; i >= s0; --i) {
-    R nxt = dm[i + 1];
-    if (rabs(nxt) < tiny) nxt = -tiny;
-    dm[i] = -lam - qdiv(b[i] * b[i], nxt);
-  }
-  int rr = s0;
-  R best = rabs(dp[s0] + dm[s0] + lam);
-  for (int i = s0 + 1; i < e0; ++i) {
-    const R g = rabs(dp[i] + dm[i] + lam);
+    R q = nxt;
+    if (rabs(q) < tiny) q = -tiny;
+    nxt = -lam - qdiv(b[i] * b[i], q);
+    dm[(size_t)i * stride] = nxt;
+    const R g = rabs(dp[(size_t)i * stride] + nxt + lam);
     if (g < best) {
       best = g;
       rr = i;
@@ -258,14 +296,14 @@ __device__ void twisted_vector(const R* b, int p, int s0, int e0, R lam, R tiny,
   R z = 1;
   if ((rr & 1) == odd) w[rr >> 1] = z;
   for (int i = rr - 1; i >= s0; --i) {
-    R d = dp[i];
+    R d = dp[(size_t)i * stride];
     if (rabs(d) < tiny) d = -tiny;
     z = -qdiv(b[i], d) * z;
     if ((i & 1) == odd) w[i >> 1] = z;
   }
   z = 1;
   for (int i = rr + 1; i < e0; ++i) {
-    R d = dm[i];
+    R d = dm[(size_t)i * stride];
     if (rabs(d) < tiny) d = -tiny;
     z = -qdiv(b[i - 1], d) * z;
     if ((i & 1) == odd) w[i >> 1] = z;
@@ -300,6 +338,69 @@ __device__ void owning_block(const R* b2, int N, const R* sig, int t, R delta, R
     }
     occ += inwin;
     bs = e;
+  }
+}
+
+// Cholesky-QR twice over the rows of W (k x p, row stride ldw): G = W W^T, G = L L^T,
+// W <- L^{-1} W. Row t of the result depends only on rows 0..t (Gram-Schmidt order),
+// so the leading singular vectors are kept as computed. A pivot below 1e-6 of its
+// diagonal (a row that is numerically a combination of earlier rows) counts as a
+// collapse. G: k x k shared scratch.
+template <class R, int NT>
+__device__ void orthonormalize_rows_chol(R* W, int ldw, int k, int p, R* G, int* collapsed) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int pass = 0; pass < 2; ++pass) {
+    // G = W W^T (lower triangle)
+    for (int e = tid; e < k * k; e += NT) {
+      const int a = e / k, b = e - a * k;
+      if (b > a) continue;
+      R acc = 0;
+      const R* wa = W + (size_t)a * ldw;
+      const R* wb = W + (size_t)b * ldw;
+#pragma unroll 4
+      for (int q = 0; q < p; ++q) acc += wa[q] * wb[q];
+      G[a * k + b] = acc;
+    }
+    __syncthreads();
+    // in-place Cholesky (lower), one warp
+    if (warp == 0) {
+      for (int j = 0; j < k; ++j) {
+        R d = G[j * k + j];
+        for (int u = lane; u < j; u += 32) {
+          const R l = G[j * k + u];
+          d -= l * l;  // partial, reduced below
+        }
+        // reduce the partial subtraction across lanes
+        R part = G[j * k + j] - d;
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        const R diag = G[j * k + j];
+        R piv = diag - part;
+        if (lane == 0 && !(piv > R(1e-6) * diag)) {
+          ++*collapsed;
+        }
+        if (!(piv > R(0))) piv = diag > R(0) ? diag * R(1e-30) : R(1e-30);
+        const R ljj = sqrt(piv);
+        __syncwarp();
+        for (int i = j + 1 + lane; i < k; i += 32) {
+          R v = G[i * k + j];
+          for (int u = 0; u < j; ++u) v -= G[i * k + u] * G[j * k + u];
+          G[i * k + j] = v / ljj;
+        }
+        __syncwarp();
+        if (lane == 0) G[j * k + j] = ljj;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // W <- L^{-1} W, one thread per column
+    for (int q = tid; q < p; q += NT) {
+      for (int t = 0; t < k; ++t) {
+        R v = W[(size_t)t * ldw + q];
+        for (int u = 0; u < t; ++u) v -= G[t * k + u] * W[(size_t)u * ldw + q];
+        W[(size_t)t * ldw + q] = v / G[t * k + t];
+      }
+    }
+    __syncthreads();
   }
 }
 

@@ -60,3 +60,21 @@ def random_unitary4(seed):
     rng = np.random.default_rng(30_000 + seed)
     z = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))
     return z  # the caller orthonormalises (QR) if it needs a unitary
+
+
+def random_right_canonical_mps(n, chi, seed):
+    """Timing/profiling input only: right-canonical random site tensors (QR of complex
+    Gaussians) at the largest ranks for (n, chi), with decaying positive lambda of unit
+    norm per bond. The lambda are not the Schmidt numbers of this state."""
+    rng = np.random.default_rng(40_000 + seed)
+    r = [1] + full_ranks(n, chi) + [1]
+    B = []
+    for k in range(n):
+        g = rng.normal(size=(2 * r[k + 1], r[k])) + 1j * rng.normal(size=(2 * r[k + 1], r[k]))
+        q, _ = np.linalg.qr(g)
+        B.append(q.conj().T.reshape(r[k], 2, r[k + 1]))
+    lam = []
+    for b in range(n - 1):
+        l = np.sort(np.exp(-np.arange(r[b + 1]) / 8.0) * rng.uniform(0.5, 1.0, size=r[b + 1]))[::-1]
+        lam.append(l / np.linalg.norm(l))
+    return B, lam
