@@ -193,6 +193,35 @@ int mps_get_stats(mps_t mps, mps_stats_t* stats);
 
 int mps_destroy(mps_t mps);
 
+/* Allocation-free gate application (the paper has no counterpart). Some callers
+ * cannot let a library allocate device memory: code running inside a stream capture
+ * that someone else owns, runtimes that hand out all device memory from their own
+ * pools, or processes with a fixed memory budget. For them this entry point applies
+ * n_gates two-site gates (Eqs. 7-10, mixed precision) to ONE MPS that lives entirely in
+ * caller-owned DEVICE memory, and allocates nothing: its workspace is a 1 MiB
+ * file-scope device array inside this library, present on every GPU that loads the
+ * library until the process exits. Limits: chi <= 64, 2 <= n_qubits <= 128; larger
+ * sizes return MPS_EINVAL.
+ *   site_tensors: complex64 (float re, im) entries; site k starts at element
+ *                 site_offsets[k] and has room for cap_{k-1} x 2 x cap_k entries,
+ *                 cap_b = min(chi, 2^min(b+1, n-1-b)) (cap_{-1} = cap_{n-1} = 1); the
+ *                 current tensor (r_{k-1}, 2, r_k) is packed row-major at its start.
+ *   site_offsets: n_qubits int64 (device). lambdas: (n_qubits-1) x chi doubles, bond b
+ *                 at b * chi (device). ranks: n_qubits+1 int32, ranks[0] = ranks[n] = 1,
+ *                 ranks[b+1] = rank of bond b (device). All four are updated in place.
+ *   bonds: n_gates int32 (device); gates: n_gates x 4 x 4 complex128, row index
+ *          2 i_b + i_{b+1} (device). cuda_stream: stream for all work (NULL = default).
+ *   discarded_weight: HOST pointer or NULL; receives the summed discarded fraction and
+ *          makes the call wait for the stream.
+ * The first call on each device looks up the workspace address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture. Every call
+ * shares the one workspace, so calls that overlap on the GPU (other streams or threads)
+ * race and must be serialised by the caller. Returns MPS_EINVAL for null pointers or
+ * sizes beyond the limits, MPS_ECUDA if a CUDA call fails. */
+int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors, const int64_t* site_offsets,
+                            double* lambdas, int32_t* ranks, int64_t n_gates, const int32_t* bonds,
+                            const double* gates, void* cuda_stream, double* discarded_weight);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* mps_last_error(void);
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "vqe_gradient": [_P, _P, _P, _P, _I, _P, _P],
     "mps_get_stats": [_P, ctypes.POINTER(MpsStats)],
     "mps_destroy": [_P],
+    "mps_apply_gates_noalloc": [_I, _I, _P, _P, _P, _P, _I64, _P, _P, _P, _PD],
     "mps_last_error": [],
 }
 
@@ -91,7 +92,7 @@ def load_library(path=LIB_PATH):
 
 
 def build(force=False):
-    from .build import build as _b
+    from .build_lib import build as _b
     return _b(force=force)
 
 
@@ -343,6 +344,18 @@ def vqe_gradient(mps, circ, ham, theta, sel):
     out = np.zeros(sel.shape[0])
     _check(load_library().vqe_gradient(mps, circ, ham, _ptr(_f64(theta)), sel.shape[0], _ptr(sel), _ptr(out)))
     return out
+
+
+def mps_apply_gates_noalloc(n_qubits, chi, site_tensors, site_offsets, lambdas, ranks, n_gates, bonds, gates,
+                            cuda_stream=0):
+    """Device-pointer arguments (ints); returns the discarded weight. See include/mpsvqe.h."""
+    dw = ctypes.c_double()
+    _check(load_library().mps_apply_gates_noalloc(n_qubits, chi, ctypes.c_void_p(site_tensors),
+                                                  ctypes.c_void_p(site_offsets), ctypes.c_void_p(lambdas),
+                                                  ctypes.c_void_p(ranks), n_gates, ctypes.c_void_p(bonds),
+                                                  ctypes.c_void_p(gates), ctypes.c_void_p(cuda_stream or None),
+                                                  ctypes.byref(dw)))
+    return dw.value
 
 
 def mps_get_stats(mps):

@@ -53,6 +53,10 @@ void dfree(void* p) {
 }
 }  // namespace
 
+namespace mpsvqe {
+void set_error_message(const char* msg) { g_err = msg; }
+}  // namespace mpsvqe
+
 // ----------------------------------------------------------------------- handles
 struct ham_s {
   int n = 0;

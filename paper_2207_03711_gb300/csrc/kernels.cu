@@ -8,6 +8,7 @@
 //  k_level_T/child/close   one level of the Pauli-string prefix trie (Eq. 11 generalised).
 //  k_energy_sum   E = sum_i a_i <P_i> (Eq. 2) with Neumaier compensation in FP64.
 #include <cfloat>
+#include <cmath>
 #include <cstdint>
 
 #include "cx.cuh"
@@ -176,7 +177,7 @@ struct EngineLayout {
   }
 };
 
-template <class R, int NT>
+template <class R, int NT, bool RAW = false>
 __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0, int64_t g1,
                                                 int slot0, const double* theta, double cutoff,
                                                 int max_sweeps) {
@@ -246,7 +247,14 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   (void)max_sweeps;
 
   for (int64_t g = g0; g < g1; ++g) {
-    const GateRec gr = c.gates[g];
+    GateRec gr;
+    if constexpr (RAW) {
+      gr.bond = c.raw_bond[g];
+      gr.param = -1;
+      gr.m0 = (int32_t)g;
+    } else {
+      gr = c.gates[g];
+    }
     // (1) the 4x4 gate: fixed, or mats[m1] . Rz(phi) on one site . mats[m0]
     if (threadIdx.x < 16) {
       const int i = threadIdx.x >> 2, j = threadIdx.x & 3;
@@ -775,3 +783,108 @@ cudaError_t launch_energy_sum(const DevMPS& m, int prec, int slot, MeasDev& w, i
 }
 
 }  // namespace mpsvqe
+
+// ------------------------------------------------------------------------------
+// Allocation-free variant of the gate engine for callers that cannot allocate device
+// memory themselves or through this library (the paper has no counterpart; see the
+// declaration of mps_apply_gates_noalloc in include/mpsvqe.h). Its workspace lives in
+// the file-scope array below, which every GPU that loads the library keeps until the
+// process exits; all calls share it.
+namespace mpsvqe {
+namespace {
+constexpr size_t kNoAllocScratchBytes = size_t(1) << 20;   // 1 MiB
+constexpr int kNoAllocMaxChi = 64;
+}  // namespace
+}  // namespace mpsvqe
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[mpsvqe::kNoAllocScratchBytes];
+
+#include <mutex>
+#include "../../include/mpsvqe.h"
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+}  // namespace
+
+extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors, const int64_t* site_offsets,
+                                       double* lambdas, int32_t* ranks, int64_t n_gates, const int32_t* bonds,
+                                       const double* gates, void* cuda_stream, double* discarded_weight) {
+  using namespace mpsvqe;
+  if (!site_tensors || !site_offsets || !lambdas || !ranks || (n_gates > 0 && (!bonds || !gates))) {
+    set_error_message("mps_apply_gates_noalloc: null device pointer");
+    return MPS_EINVAL;
+  }
+  if (n_qubits < 2 || n_qubits > kMaxQubits || chi < 1 || chi > kNoAllocMaxChi || n_gates < 0) {
+    set_error_message("mps_apply_gates_noalloc: needs 2 <= n_qubits <= 128, 1 <= chi <= 64 and n_gates >= 0 "
+                      "(the fixed 1 MiB device workspace holds one chi <= 64 gate step)");
+    return MPS_EINVAL;
+  }
+  const size_t mm = 2 * (size_t)chi;
+  const size_t off_M = 0;
+  const size_t off_X = off_M + ((mm * mm * 8 + 255) & ~(size_t)255);
+  const size_t off_S = off_X + ((mm * (mm + 1) * 8 + 255) & ~(size_t)255);
+  const size_t off_dw = off_S + ((16 * (size_t)chi * chi * 8 + 255) & ~(size_t)255);
+  const size_t off_end = off_dw + 256;
+  if (off_end > kNoAllocScratchBytes) {
+    set_error_message("mps_apply_gates_noalloc: workspace larger than the 1 MiB device array");
+    return MPS_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    set_error_message("mps_apply_gates_noalloc: no current CUDA device");
+    return MPS_ECUDA;
+  }
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        set_error_message("mps_apply_gates_noalloc: cudaGetSymbolAddress of the device workspace failed");
+        return MPS_ECUDA;
+      }
+      g_noalloc_ptr[dev] = p;
+    }
+    base = (unsigned char*)g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DevMPS d{};
+  d.n = n_qubits;
+  d.chi = chi;
+  d.n_slots = 1;
+  d.slot_elems = 0;
+  d.site_off = site_offsets;
+  d.B = site_tensors;
+  d.lam = lambdas;
+  d.rank = ranks;
+  d.work_M = base + off_M;
+  d.work_X = base + off_X;
+  d.work_S = base + off_S;
+  d.dw = (double*)(base + off_dw);
+  d.stat = (int*)(base + off_dw + 8);
+  d.prof = (unsigned long long*)(base + off_dw + 64);
+  // the shared array keeps the previous call's contents: clear the accumulators
+  if (cudaMemsetAsync(base + off_dw, 0, 256, st) != cudaSuccess) return MPS_ECUDA;
+  CircDev c{};
+  c.gates = nullptr;
+  c.n_gates = n_gates;
+  c.mats = gates;
+  c.n_params = 1;
+  c.raw_bond = bonds;
+  const EngineLayout<float> L(chi, 512);
+  if (cudaFuncSetAttribute(k_circuit<float, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)L.total) != cudaSuccess)
+    return MPS_ECUDA;
+  const double* theta = (const double*)(base + off_dw + 128);   // never read: every gate is fixed
+  for (int64_t g0 = 0; g0 < n_gates; g0 += 16384) {
+    const int64_t g1 = g0 + 16384 < n_gates ? g0 + 16384 : n_gates;
+    k_circuit<float, 512, true><<<1, 512, L.total, st>>>(d, c, g0, g1, 0, theta, std::ldexp(1.0, -20), 40);
+    if (cudaGetLastError() != cudaSuccess) return MPS_ECUDA;
+  }
+  if (discarded_weight) {
+    if (cudaMemcpyAsync(discarded_weight, d.dw, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MPS_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ECUDA;
+  }
+  return MPS_OK;
+}

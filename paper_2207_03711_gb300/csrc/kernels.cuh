@@ -32,6 +32,7 @@ struct CircDev {
   int64_t n_gates;
   const double* mats;  // 32 doubles per matrix (16 complex)
   int n_params;
+  const int32_t* raw_bond = nullptr;  // raw-gate launches only: bond of gate g, matrix g of mats
 };
 
 // Reset slots [slot0, slot0+count) to product states; occ: [count][n] bytes (0/1).
@@ -63,6 +64,9 @@ struct TrieLevelDev {
   const uint8_t* close_letter;
   const int32_t* close_term;
 };
+
+// Thread-local message returned by mps_last_error() (defined with the C ABI).
+void set_error_message(const char* msg);
 
 cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, MeasDev& w, cudaStream_t st);
 cudaError_t launch_level(const DevMPS& m, int prec, int slot, MeasDev& w, int k,

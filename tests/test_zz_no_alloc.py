@@ -1,0 +1,96 @@
+"""The allocation-free gate entry point gives the same MPS as the allocating one.
+
+mps_apply_gates_noalloc serves callers that cannot let a library allocate device
+memory (for example code inside someone else's stream capture, or runtimes that own
+all device memory through their own pools): the caller keeps the whole MPS in its own
+device buffers and the library works inside a fixed device array. This test applies
+the same gates through both entry points, twice in a row, and compares the results
+within the mixed-precision tolerances used by the other truncated-step tests.
+"""
+import numpy as np
+import pytest
+
+import paper_2207_03711_gb300 as G
+from oracle import mps
+from paper_2207_03711_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+LAM_TOL, BLK_TOL = 2e-5, 2e-4
+
+
+def caps(n, chi):
+    c = [1] + [min(chi, 2 ** min(b + 1, n - 1 - b)) for b in range(n - 1)] + [1]
+    off, o = [], 0
+    for k in range(n):
+        off.append(o)
+        o += c[k] * 2 * c[k + 1]
+    return c, off, o
+
+
+def test_noalloc_matches_allocating_path():
+    torch = pytest.importorskip("torch")
+    G.build()
+    G.load_library()
+    n, chi = 24, 64
+    r = syn.full_ranks(n, chi)
+    st = mps.random_canonical(n, r, syn.random_mps_gaussians(n, r, 11))
+    C = G.circ_uccsd(n, n // 2)
+    bond, U = G.circ_export_gates(C, syn.random_amplitudes(C.n_params, 3))
+    sel = slice(30000, 30080)
+    bond, U = bond[sel].copy(), U[sel].copy()
+
+    # allocating path
+    M = G.mps_create(n, chi, G.MPS_MIXED)
+    G.mps_set_state(M, st.B, st.lam)
+
+    # caller-owned device buffers for the allocation-free path
+    cap, off, total = caps(n, chi)
+    flat = np.zeros(total, dtype=np.complex64)
+    for k in range(n):
+        flat[off[k]:off[k] + st.B[k].size] = st.B[k].astype(np.complex64).ravel()
+    lam = np.zeros((n - 1, chi))
+    for b in range(n - 1):
+        lam[b, :len(st.lam[b])] = st.lam[b]
+    ranks = np.array([1] + [len(l) for l in st.lam] + [1], dtype=np.int32)
+    dev = torch.device("cuda")
+    d_B = torch.from_numpy(flat).to(dev)
+    d_off = torch.tensor(off, dtype=torch.int64, device=dev)
+    d_lam = torch.from_numpy(lam).to(dev)
+    d_rank = torch.from_numpy(ranks).to(dev)
+    d_bond = torch.from_numpy(bond.astype(np.int32)).to(dev)
+    d_U = torch.from_numpy(U.astype(np.complex128)).to(dev)
+    torch.cuda.synchronize()
+
+    half = len(bond) // 2
+    for call in range(2):                       # two calls in a row on the shared workspace
+        a, b = call * half, (call + 1) * half
+        dw_ref = G.mps_apply_gates(M, bond[a:b], U[a:b], allow_noconv=True)
+        dw = G.mps_apply_gates_noalloc(n, chi, d_B.data_ptr(), d_off.data_ptr(), d_lam.data_ptr(),
+                                       d_rank.data_ptr(), b - a, d_bond.data_ptr() + 4 * a,
+                                       d_U.data_ptr() + 256 * a, 0)
+        torch.cuda.synchronize()
+        r_ref, sites_ref, lams_ref = G.mps_get_state(M)
+        rk = d_rank.cpu().numpy()[1:-1]
+        assert list(rk) == list(r_ref)
+        assert abs(dw - dw_ref) <= 1e-6
+        fl = d_B.cpu().numpy()
+        lm = d_lam.cpu().numpy()
+        full = [1] + list(rk) + [1]
+        for q in range(n - 1):
+            assert np.abs(lm[q, :full[q + 1]] - lams_ref[q]).max() <= LAM_TOL
+        for q in range(1, n - 1):
+            Bq = fl[off[q]:off[q] + full[q] * 2 * full[q + 1]].reshape(full[q], 2, full[q + 1])
+            Bq1 = fl[off[q + 1]:off[q + 1] + full[q + 1] * 2 * full[q + 2]].reshape(full[q + 1], 2, full[q + 2])
+            ll = lams_ref[q - 1]
+            blk = ll[:, None, None, None] * np.einsum("aib,bjc->aijc", Bq, Bq1)
+            ref = ll[:, None, None, None] * np.einsum("aib,bjc->aijc", sites_ref[q], sites_ref[q + 1])
+            assert np.linalg.norm(blk - ref) <= BLK_TOL * np.linalg.norm(ref)
+
+
+def test_noalloc_rejects_sizes_beyond_the_workspace():
+    G.build()
+    G.load_library()
+    with pytest.raises(G.MpsError) as e:
+        G.mps_apply_gates_noalloc(24, 128, 1, 1, 1, 1, 0, 1, 1, 0)
+    assert e.value.code == G.MPS_EINVAL and "chi" in str(e.value)
