@@ -166,7 +166,7 @@ struct EngineLayout {
           (8 + 4) * mmax + 16 + sizeof(R) * nt + 4 * (size_t)chi + 16;
     svd = (svd + 255) & ~(size_t)255;
     w_bytes = sizeof(R) * ((size_t)chi * (mmax + 1) + (size_t)chi * chi);   // W rows + Gram
-    t_bytes = sizeof(Cx<R>) * (mmax + 1) * mmax;
+    t_bytes = sizeof(Cx<R>) * (mmax + 16) * mmax;
     // the static site-update GEMM tiles (64x17 + 16x65 complex) share the 227 KB
     const size_t cap = 226 * 1024 - sizeof(Cx<R>) * (64 * 17 + 16 * 65) - 512;
     w_off = head + svd;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   __shared__ Cx<R> gA[64][17];
   __shared__ Cx<R> gB[16][65];
   R* Wv = L.w_smem ? (R*)(smem + L.w_off) : (R*)((double*)m.work_S + (size_t)s * 16 * chi * chi + 8 * chi * chi);
-  Cx<R>* T = L.t_smem ? (Cx<R>*)(smem + L.t_off) : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 1);
+  Cx<R>* T = L.t_smem ? (Cx<R>*)(smem + L.t_off) : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 16);
   const double* th = theta + (size_t)blockIdx.x * c.n_params;
 
   int st_max_iters = 0, st_max_rank = 1, st_bad = 0;
@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   }
   __syncthreads();
   unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  unsigned long long bsub[4] = {0, 0, 0, 0};   // bidiagonalisation sub-phases
   double alg_flops = 0.0;  // algorithmic real flops of the gate steps (see flops_per_gate)
   long long t_mark = clock64();
 #define PHASE(i)                                   \
@@ -281,7 +282,10 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     const int rl = rank[bond], rm = rank[bond + 1], rr = rank[bond + 2];
     const int mrows = 2 * rl, ncol = 2 * rr;
     const bool tall = mrows >= ncol;
-    const int tr = tall ? mrows : ncol, tp = tall ? ncol : mrows, ld = tr + 1;
+    const int tr = tall ? mrows : ncol, tp = tall ? ncol : mrows;
+    // leading dimension = 4 (mod 16) complex entries: column walks by 8-lane groups and
+    // row walks over 8 columns x 4 rows both touch each shared-memory bank pair twice
+    const int ld = tr + ((20 - (tr & 15)) & 15);
     Cx<R>* Bn = Bslot + m.site_off[bond];
     Cx<R>* Bn1 = Bslot + m.site_off[bond + 1];
     const double* laml = bond > 0 ? lam + (size_t)(bond - 1) * chi : nullptr;
@@ -333,7 +337,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     PHASE(0);
     // (3) Eq. (9): bidiagonalise T = Q B P^H (B real); the reflector vectors are staged
     //     in the (not yet used) singular-vector buffer
-    bidiagonalize<R, NT>(T, ld, tr, tp, dd, ee, tauL, tauR, (Cx<R>*)Wv, (Cx<R>*)Wv + mmax);
+    bidiagonalize<R, NT>(T, ld, tr, tp, dd, ee, tauL, tauR, (Cx<R>*)Wv, (Cx<R>*)Wv + mmax, bsub);
     PHASE(1);
     // Golub-Kahan tridiagonal off-diagonal b = (d0, e0, d1, e1, ..., d_{p-1})
     for (int i = threadIdx.x; i < 2 * tp - 1; i += NT) {
@@ -342,13 +346,14 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
       b2[i] = v * v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       R smax = 0;
-      for (int i = 0; i < 2 * tp; ++i) {
+      for (int i = threadIdx.x; i < 2 * tp; i += 32) {
         const R left = i > 0 ? rabs(bb[i - 1]) : R(0), right = i < 2 * tp - 1 ? rabs(bb[i]) : R(0);
         smax = fmax(smax, left + right);
       }
-      coef[0] = smax;
+      for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+      if (threadIdx.x == 0) coef[0] = smax;
     }
     __syncthreads();
     const R smax = coef[0];
@@ -364,14 +369,18 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     const bool fp64 = sizeof(R) == 8;
     const int iters = iters_of[kk - 1];
     bisect_singular_values<R, NT>(b2, tp, smax, kk, iters, sig, lo, hi, cnt, xs, grid);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      // sig is descending: k = number of leading values above cutoff * sig_0
       const R s0 = sig[0];
-      int k = 0;
-      while (k < kk && sig[k] > (R)cutoff * s0 && sig[k] > R(0)) ++k;
-      if (k == 0) k = 1;
-      misc[0] = k;
-      st_max_rank = max(st_max_rank, k);
-      st_max_iters = max(st_max_iters, iters);
+      int cntk = 0;
+      for (int t = threadIdx.x; t < kk; t += 32) cntk += (sig[t] > (R)cutoff * s0 && sig[t] > R(0));
+      for (int o = 16; o > 0; o >>= 1) cntk += __shfl_xor_sync(0xffffffffu, cntk, o);
+      if (threadIdx.x == 0) {
+        const int k = cntk > 0 ? cntk : 1;
+        misc[0] = k;
+        st_max_rank = max(st_max_rank, k);
+        st_max_iters = max(st_max_iters, iters);
+      }
     }
     __syncthreads();
     const int k = misc[0];
@@ -391,7 +400,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     if (threadIdx.x == 0) misc[1] = 0;
     __syncthreads();
     PHASE(3);
-    orthonormalize_rows_chol<R, NT>(Wv, mmax + 1, k, tp, Wv + (size_t)chi * (mmax + 1), &misc[1]);
+    orthonormalize_rows_block<R, NT>(Wv, mmax + 1, k, tp, Wv + (size_t)chi * (mmax + 1), &misc[1]);
     PHASE(4);
     Cx<R>* xout = (Cx<R>*)scratch;               // k x ncol right singular vectors v_t
     int kf = k;                                  // kept count of the path taken
@@ -521,6 +530,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
 #undef PHASE
   if (threadIdx.x == 0) {
     for (int i = 0; i < 7; ++i) m.prof[s * 8 + i] += ph[i];
+    for (int i = 0; i < 4; ++i) m.prof[(size_t)m.n_slots * 8 + s * 4 + i] += bsub[i];
     m.prof[s * 8 + 7] = __double_as_longlong(__longlong_as_double(m.prof[s * 8 + 7]) + alg_flops);
     m.dw[s] += dw_acc;
     int* stt = m.stat + s * 4;
@@ -823,7 +833,7 @@ extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors
   const size_t mm = 2 * (size_t)chi;
   const size_t off_M = 0;
   const size_t off_X = off_M + ((mm * mm * 8 + 255) & ~(size_t)255);
-  const size_t off_S = off_X + ((mm * (mm + 1) * 8 + 255) & ~(size_t)255);
+  const size_t off_S = off_X + ((mm * (mm + 16) * 8 + 255) & ~(size_t)255);
   const size_t off_dw = off_S + ((16 * (size_t)chi * chi * 8 + 255) & ~(size_t)255);
   const size_t off_end = off_dw + 256;
   if (off_end > kNoAllocScratchBytes) {
@@ -863,7 +873,7 @@ extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors
   d.work_S = base + off_S;
   d.dw = (double*)(base + off_dw);
   d.stat = (int*)(base + off_dw + 8);
-  d.prof = (unsigned long long*)(base + off_dw + 64);
+  d.prof = (unsigned long long*)(base + off_dw + 64);   // 8 phase + 4 bidiagonalisation counters
   // the shared array keeps the previous call's contents: clear the accumulators
   if (cudaMemsetAsync(base + off_dw, 0, 256, st) != cudaSuccess) return MPS_ECUDA;
   CircDev c{};
@@ -876,7 +886,7 @@ extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors
   if (cudaFuncSetAttribute(k_circuit<float, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)L.total) != cudaSuccess)
     return MPS_ECUDA;
-  const double* theta = (const double*)(base + off_dw + 128);   // never read: every gate is fixed
+  const double* theta = (const double*)(base + off_dw + 224);   // never read: every gate is fixed
   for (int64_t g0 = 0; g0 < n_gates; g0 += 16384) {
     const int64_t g1 = g0 + 16384 < n_gates ? g0 + 16384 : n_gates;
     k_circuit<float, 512, true><<<1, 512, L.total, st>>>(d, c, g0, g1, 0, theta, std::ldexp(1.0, -20), 40);

@@ -20,7 +20,7 @@ struct DevMPS {
   double* lam;              // [n_slots][n-1][chi]
   int* rank;                // [n_slots][n+1]; rank[0] = rank[n] = 1, rank[b+1] = rank of bond b
   void* work_M;             // complex<R> [n_slots][(2chi)^2]  gate workspace (unscaled M)
-  void* work_X;             // complex<R> [n_slots][2chi (2chi+1)]  M' when not in smem
+  void* work_X;             // complex<R> [n_slots][2chi (2chi+16)]  M' when not in smem
   void* work_S;             // double [n_slots][16 chi^2]  SVD scratch (vectors, factorisations)
   double* dw;               // [n_slots] accumulated discarded weight
   int* stat;                // [n_slots][4]: bisection passes, collapsed vectors, max rank, error flag

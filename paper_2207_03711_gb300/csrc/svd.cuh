@@ -53,12 +53,17 @@ __device__ __forceinline__ void make_reflector(Cx<R> alpha, R xn2, Cx<R>* tau, R
 // vb, wb: shared scratch of >= r and >= p complex entries (reflector vectors).
 template <class R, int NT>
 __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R>* tauL, Cx<R>* tauR,
-                              Cx<R>* vb, Cx<R>* wb) {
+                              Cx<R>* vb, Cx<R>* wb, unsigned long long* sub = nullptr) {
+  long long tm = clock64();
+  auto mark = [&](int i) {
+    if (sub && threadIdx.x == 0) {
+      const long long now = clock64();
+      sub[i] += (unsigned long long)(now - tm);
+      tm = now;
+    }
+  };
   constexpr int EPL = sizeof(R) == 4 ? 16 : 8;   // entries per lane
-  int LPC = 8;                                     // lanes per column / row
-  while (LPC < 32 && LPC * EPL < (r > p ? r : p)) LPC <<= 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int grp = tid / LPC, l8 = tid % LPC;
   for (int k = 0; k < p; ++k) {
     // --- left reflector on column k, rows k..r-1 (warp 0)
     if (warp == 0) {
@@ -81,10 +86,15 @@ __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R
       }
     }
     __syncthreads();
+    mark(0);
     // --- apply H^H = I - conj(tau) v v^H to columns k+1..p-1
     {
       const Cx<R> ct = conj(tauL[k]);
       const int nr = r - k;
+      // lanes per column for this step: the fewest that cover the live rows
+      int lg = 0;
+      while (lg < 5 && (EPL << lg) < nr) ++lg;
+      const int LPC = 1 << lg, grp = tid >> lg, l8 = tid & (LPC - 1);
       Cx<R> v[EPL];
 #pragma unroll
       for (int e = 0; e < EPL; ++e) {
@@ -116,6 +126,7 @@ __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R
       }
     }
     __syncthreads();
+    mark(1);
     if (k >= p - 1) break;
     // --- right reflector on row k, columns k+1..p-1 (warp 0), acting on conj(row)
     if (warp == 0) {
@@ -138,10 +149,14 @@ __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R
       }
     }
     __syncthreads();
+    mark(2);
     // --- apply G = I - tau w w^H from the right to rows k+1..r-1, columns k+1..p-1
     {
       const Cx<R> t = tauR[k];
       const int nc = p - k - 1;
+      int lg = 0;
+      while (lg < 5 && (EPL << lg) < nc) ++lg;
+      const int LPC = 1 << lg, grp = tid >> lg, l8 = tid & (LPC - 1);
       Cx<R> w[EPL];
 #pragma unroll
       for (int e = 0; e < EPL; ++e) {
@@ -173,6 +188,7 @@ __device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R
       }
     }
     __syncthreads();
+    mark(3);
   }
 }
 
@@ -398,6 +414,67 @@ __device__ void orthonormalize_rows_chol(R* W, int ldw, int k, int p, R* G, int*
         R v = W[(size_t)t * ldw + q];
         for (int u = 0; u < t; ++u) v -= G[t * k + u] * W[(size_t)u * ldw + q];
         W[(size_t)t * ldw + q] = v / G[t * k + t];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Block classical Gram-Schmidt (twice) over the rows of W (k x p, row stride ldw), in
+// blocks of 8 rows: each block is projected out of all earlier rows in two passes, then
+// orthonormalised internally by one warp (modified Gram-Schmidt). Row t of the result
+// depends only on rows 0..t, so the leading singular vectors keep their directions. A
+// row whose remainder falls below 1e-3 of its norm counts as a collapse.
+// coef: >= 8 k shared scratch.
+template <class R, int NT>
+__device__ void orthonormalize_rows_block(R* W, int ldw, int k, int p, R* coef, int* collapsed) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int b0 = 0; b0 < k; b0 += 8) {
+    const int nb = min(8, k - b0);
+    for (int pass = 0; pass < 2 && b0 > 0; ++pass) {
+      // coef[u * 8 + j] = <w_u, w_{b0+j}>, 8 lanes per dot
+      const int nd = b0 * nb;
+      for (int base = 0; base < nd * 8; base += NT) {
+        const int d = (base + tid) >> 3, l = tid & 7;
+        const bool act = d < nd;
+        const int u = act ? d / nb : 0, j = act ? d - u * nb : 0;
+        R acc = 0;
+        if (act)
+          for (int q = l; q < p; q += 8) acc += W[(size_t)u * ldw + q] * W[(size_t)(b0 + j) * ldw + q];
+        for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (act && l == 0) coef[u * 8 + j] = acc;
+      }
+      __syncthreads();
+      for (int it = tid; it < nb * p; it += NT) {
+        const int j = it / p, q = it - j * p;
+        R v = W[(size_t)(b0 + j) * ldw + q];
+        for (int u = 0; u < b0; ++u) v -= coef[u * 8 + j] * W[(size_t)u * ldw + q];
+        W[(size_t)(b0 + j) * ldw + q] = v;
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      for (int j = 0; j < nb; ++j) {
+        R* wj = W + (size_t)(b0 + j) * ldw;
+        R n0 = 0;
+        for (int q = lane; q < p; q += 32) n0 += wj[q] * wj[q];
+        for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+        for (int rep = 0; rep < 2; ++rep)
+          for (int i = 0; i < j; ++i) {
+            const R* wi = W + (size_t)(b0 + i) * ldw;
+            R d = 0;
+            for (int q = lane; q < p; q += 32) d += wi[q] * wj[q];
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            for (int q = lane; q < p; q += 32) wj[q] -= d * wi[q];
+            __syncwarp();
+          }
+        R nr = 0;
+        for (int q = lane; q < p; q += 32) nr += wj[q] * wj[q];
+        for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
+        if (lane == 0 && !(nr > R(1e-6) * n0)) ++*collapsed;
+        const R inv = nr > R(0) ? R(1) / sqrt(nr) : R(0);
+        for (int q = lane; q < p; q += 32) wj[q] *= inv;
+        __syncwarp();
       }
     }
     __syncthreads();
