@@ -188,8 +188,6 @@ typedef struct {
   double alg_flops_total;  /* slot-0 algorithmic real flops of all gate steps      */
                            /* since creation (dense contraction + Golub-Reinsch    */
                            /* SVD with right vectors + site update)                */
-  double cycles_bidiag[4]; /* slot-0 cycles inside the bidiagonalisation: left    */
-                           /* reflector, left update, right reflector, right update */
 } mps_stats_t;
 int mps_get_stats(mps_t mps, mps_stats_t* stats);
 

@@ -36,7 +36,7 @@ class MpsStats(ctypes.Structure):
                 ("n_svd_noconv", ctypes.c_int64), ("ms_circuit", ctypes.c_double),
                 ("ms_measure", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("cycles", ctypes.c_double * 7), ("n_fallback", ctypes.c_int64),
-                ("alg_flops_total", ctypes.c_double), ("cycles_bidiag", ctypes.c_double * 4)]
+                ("alg_flops_total", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -363,7 +363,6 @@ def mps_get_stats(mps):
     _check(load_library().mps_get_stats(mps, ctypes.byref(s)))
     out = {k: getattr(s, k) for k, _ in MpsStats._fields_}
     out["cycles"] = list(s.cycles)
-    out["cycles_bidiag"] = list(s.cycles_bidiag)
     return out
 
 

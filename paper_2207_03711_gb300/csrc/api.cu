@@ -528,8 +528,8 @@ int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_str
   d.work_S = p;
   TRY(dalloc(&d.dw, n_slots));
   TRY(dalloc(&d.stat, (size_t)n_slots * 4));
-  TRY(dalloc(&d.prof, (size_t)n_slots * 12));
-  CU(cudaMemset(d.prof, 0, (size_t)n_slots * 12 * 8));
+  TRY(dalloc(&d.prof, (size_t)n_slots * 8));
+  CU(cudaMemset(d.prof, 0, (size_t)n_slots * 8 * 8));
   TRY(dalloc(&m->d_site_off, n));
   CU(cudaMemcpy(m->d_site_off, m->site_off.data(), n * 8, cudaMemcpyHostToDevice));
   d.site_off = m->d_site_off;
@@ -573,11 +573,9 @@ static int finish_apply(mps_s* m, double* discarded_weight) {
   double dw = 0;
   int st4[4];
   TRY(read_slot_stats(m, 0, &dw, st4));
-  unsigned long long pr[8], sub[4];
+  unsigned long long pr[8];
   CU(cudaMemcpy(pr, m->dm.prof, sizeof(pr), cudaMemcpyDeviceToHost));
-  CU(cudaMemcpy(sub, m->dm.prof + (size_t)m->n_slots * 8, sizeof(sub), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 7; ++i) m->stats.cycles[i] = (double)pr[i];
-  for (int i = 0; i < 4; ++i) m->stats.cycles_bidiag[i] = (double)sub[i];
   double fl;
   std::memcpy(&fl, &pr[7], 8);
   m->stats.alg_flops_total = fl;

@@ -177,7 +177,9 @@ struct EngineLayout {
   }
 };
 
-template <class R, int NT, bool RAW = false>
+// TS: the singular-vector area and T live in shared memory (the layout decides on the
+// host); a compile-time placement lets the compiler use shared-memory instructions.
+template <class R, int NT, bool RAW = false, bool TS = true>
 __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0, int64_t g1,
                                                 int slot0, const double* theta, double cutoff,
                                                 int max_sweeps) {
@@ -213,8 +215,8 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   int* iters_of = (int*)(grid + NT);         // bisection passes for kk = 1..chi
   __shared__ Cx<R> gA[64][17];
   __shared__ Cx<R> gB[16][65];
-  R* Wv = L.w_smem ? (R*)(smem + L.w_off) : (R*)((double*)m.work_S + (size_t)s * 16 * chi * chi + 8 * chi * chi);
-  Cx<R>* T = L.t_smem ? (Cx<R>*)(smem + L.t_off) : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 16);
+  R* Wv = TS ? (R*)(smem + L.w_off) : (R*)((double*)m.work_S + (size_t)s * 16 * chi * chi + 8 * chi * chi);
+  Cx<R>* T = TS ? (Cx<R>*)(smem + L.t_off) : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 16);
   const double* th = theta + (size_t)blockIdx.x * c.n_params;
 
   int st_max_iters = 0, st_max_rank = 1, st_bad = 0;
@@ -233,7 +235,6 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   }
   __syncthreads();
   unsigned long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  unsigned long long bsub[4] = {0, 0, 0, 0};   // bidiagonalisation sub-phases
   double alg_flops = 0.0;  // algorithmic real flops of the gate steps (see flops_per_gate)
   long long t_mark = clock64();
 #define PHASE(i)                                   \
@@ -283,9 +284,10 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     const int mrows = 2 * rl, ncol = 2 * rr;
     const bool tall = mrows >= ncol;
     const int tr = tall ? mrows : ncol, tp = tall ? ncol : mrows;
-    // leading dimension = 4 (mod 16) complex entries: column walks by 8-lane groups and
-    // row walks over 8 columns x 4 rows both touch each shared-memory bank pair twice
-    const int ld = tr + ((20 - (tr & 15)) & 15);
+    // leading dimension: 2 (mod 16) complex<float> entries, so that 16-lane column
+    // walks and 8-column x 2-row walks of a half warp hit 16 distinct bank pairs;
+    // odd for complex<double>, so that 8 consecutive columns of one row do too
+    const int ld = sizeof(R) == 4 ? tr + ((18 - (tr & 15)) & 15) : tr + ((17 - (tr & 15)) & 15);
     Cx<R>* Bn = Bslot + m.site_off[bond];
     Cx<R>* Bn1 = Bslot + m.site_off[bond + 1];
     const double* laml = bond > 0 ? lam + (size_t)(bond - 1) * chi : nullptr;
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     PHASE(0);
     // (3) Eq. (9): bidiagonalise T = Q B P^H (B real); the reflector vectors are staged
     //     in the (not yet used) singular-vector buffer
-    bidiagonalize<R, NT>(T, ld, tr, tp, dd, ee, tauL, tauR, (Cx<R>*)Wv, (Cx<R>*)Wv + mmax, bsub);
+    bidiagonalize<R, NT>(T, ld, tr, tp, dd, ee, tauL, tauR);
     PHASE(1);
     // Golub-Kahan tridiagonal off-diagonal b = (d0, e0, d1, e1, ..., d_{p-1})
     for (int i = threadIdx.x; i < 2 * tp - 1; i += NT) {
@@ -400,7 +402,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     if (threadIdx.x == 0) misc[1] = 0;
     __syncthreads();
     PHASE(3);
-    orthonormalize_rows_block<R, NT>(Wv, mmax + 1, k, tp, Wv + (size_t)chi * (mmax + 1), &misc[1]);
+    orthonormalize_rows_block<R, NT>(Wv, mmax + 1, k, tp, Wv + (size_t)chi * (mmax + 1), xs, &misc[1]);
     PHASE(4);
     Cx<R>* xout = (Cx<R>*)scratch;               // k x ncol right singular vectors v_t
     int kf = k;                                  // kept count of the path taken
@@ -426,15 +428,21 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
         for (int jr = nref - 1; jr >= 0; --jr) {
           const int start = tall ? jr + 1 : jr;
           const Cx<R> tau = tall ? tauR[jr] : tauL[jr];
+          const Cx<R> scj = tall ? T[(size_t)(jr + 1) * ld + jr] : T[(size_t)jr * ld + jr];
+          // entry e covers q in [e LV, e LV + LV); entries wholly above the reflector's
+          // start are zero and skipped (the test is uniform over the block)
           Cx<R> hv[16];
           Cx<R> sdot = cx<R>(0, 0);
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            const int q = l + e * LV;
             hv[e] = cx<R>(0, 0);
-            if (q > start && q < ncol) hv[e] = tall ? T[(size_t)q * ld + jr] : T[(size_t)jr * ld + q];
-            if (q == start) hv[e] = cx<R>(1, 0);
-            cmac_conj(sdot, hv[e], x[e]);
+            if ((e + 1) * LV > start) {
+              const int q = l + e * LV;
+              if (q > start && q < ncol)
+                hv[e] = tall ? conj(T[(size_t)q * ld + jr]) * scj : T[(size_t)jr * ld + q] * scj;
+              if (q == start) hv[e] = cx<R>(1, 0);
+              cmac_conj(sdot, hv[e], x[e]);
+            }
           }
           for (int o = 1; o < LV; o <<= 1) {
             sdot.x += __shfl_xor_sync(0xffffffffu, sdot.x, o, LV);
@@ -442,7 +450,8 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
           }
           const Cx<R> f = tau * sdot;
 #pragma unroll
-          for (int e = 0; e < 16; ++e) x[e] = x[e] - f * hv[e];
+          for (int e = 0; e < 16; ++e)
+            if ((e + 1) * LV > start) x[e] = x[e] - f * hv[e];
         }
         if (act) {
 #pragma unroll
@@ -530,7 +539,6 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
 #undef PHASE
   if (threadIdx.x == 0) {
     for (int i = 0; i < 7; ++i) m.prof[s * 8 + i] += ph[i];
-    for (int i = 0; i < 4; ++i) m.prof[(size_t)m.n_slots * 8 + s * 4 + i] += bsub[i];
     m.prof[s * 8 + 7] = __double_as_longlong(__longlong_as_double(m.prof[s * 8 + 7]) + alg_flops);
     m.dw[s] += dw_acc;
     int* stt = m.stat + s * 4;
@@ -546,10 +554,17 @@ static cudaError_t launch_circ_t(const DevMPS& m, const CircDev& c, int64_t g0, 
                                  int slot0, int count, const double* theta, double cutoff,
                                  int max_sweeps, cudaStream_t st) {
   const EngineLayout<R> L(m.chi, NT);
-  cudaError_t e = cudaFuncSetAttribute(k_circuit<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)L.total);
-  if (e != cudaSuccess) return e;
-  k_circuit<R, NT><<<count, NT, L.total, st>>>(m, c, g0, g1, slot0, theta, cutoff, max_sweeps);
+  if (L.w_smem && L.t_smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_circuit<R, NT, false, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    k_circuit<R, NT, false, true><<<count, NT, L.total, st>>>(m, c, g0, g1, slot0, theta, cutoff, max_sweeps);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_circuit<R, NT, false, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    if (e != cudaSuccess) return e;
+    k_circuit<R, NT, false, false><<<count, NT, L.total, st>>>(m, c, g0, g1, slot0, theta, cutoff, max_sweeps);
+  }
   return cudaGetLastError();
 }
 
@@ -873,7 +888,7 @@ extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors
   d.work_S = base + off_S;
   d.dw = (double*)(base + off_dw);
   d.stat = (int*)(base + off_dw + 8);
-  d.prof = (unsigned long long*)(base + off_dw + 64);   // 8 phase + 4 bidiagonalisation counters
+  d.prof = (unsigned long long*)(base + off_dw + 64);
   // the shared array keeps the previous call's contents: clear the accumulators
   if (cudaMemsetAsync(base + off_dw, 0, 256, st) != cudaSuccess) return MPS_ECUDA;
   CircDev c{};
@@ -883,13 +898,17 @@ extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors
   c.n_params = 1;
   c.raw_bond = bonds;
   const EngineLayout<float> L(chi, 512);
-  if (cudaFuncSetAttribute(k_circuit<float, 512, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (!(L.w_smem && L.t_smem)) {   // holds for every chi <= 64 in complex64
+    set_error_message("mps_apply_gates_noalloc: gate workspace does not fit in shared memory");
+    return MPS_EINVAL;
+  }
+  if (cudaFuncSetAttribute(k_circuit<float, 512, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)L.total) != cudaSuccess)
     return MPS_ECUDA;
-  const double* theta = (const double*)(base + off_dw + 224);   // never read: every gate is fixed
+  const double* theta = (const double*)(base + off_dw + 128);   // never read: every gate is fixed
   for (int64_t g0 = 0; g0 < n_gates; g0 += 16384) {
     const int64_t g1 = g0 + 16384 < n_gates ? g0 + 16384 : n_gates;
-    k_circuit<float, 512, true><<<1, 512, L.total, st>>>(d, c, g0, g1, 0, theta, std::ldexp(1.0, -20), 40);
+    k_circuit<float, 512, true, true><<<1, 512, L.total, st>>>(d, c, g0, g1, 0, theta, std::ldexp(1.0, -20), 40);
     if (cudaGetLastError() != cudaSuccess) return MPS_ECUDA;
   }
   if (discarded_weight) {

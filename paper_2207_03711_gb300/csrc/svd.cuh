@@ -10,8 +10,8 @@
 //
 // Conventions: the reflector H = I - tau v v^H (v_0 = 1) satisfies H^H x = beta e_1
 // with beta real. T (r x p, r >= p, column-major, leading dimension ld) is reduced
-// to T = Q B P^H with Q = H_0 H_1 ... (left reflectors stored below the diagonal),
-// P = G_0 G_1 ... (right reflectors stored right of the superdiagonal).
+// to T = Q B P^H with Q = H_0 H_1 ... and P = G_0 G_1 ...; reflector k's tail is
+// (unscaled tail stored in T) x (scale stored over its pivot), see bidiagonalize.
 #pragma once
 #include "cx.cuh"
 
@@ -46,150 +46,158 @@ __device__ __forceinline__ void make_reflector(Cx<R> alpha, R xn2, Cx<R>* tau, R
 }
 
 // Householder bidiagonalisation, NT threads, T in shared (or global) memory. dd[k]
-// (diagonal) and ee[k] (superdiagonal) receive the real entries; tauL/tauR the
-// reflector factors. Each column (left update) or row (right update) is handled by 8
-// lanes that keep their 16 entries in registers between the dot product and the
-// rank-1 update, so every element is read and written once per half step.
-// vb, wb: shared scratch of >= r and >= p complex entries (reflector vectors).
-template <class R, int NT>
-__device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R>* tauL, Cx<R>* tauR,
-                              Cx<R>* vb, Cx<R>* wb, unsigned long long* sub = nullptr) {
-  long long tm = clock64();
-  auto mark = [&](int i) {
-    if (sub && threadIdx.x == 0) {
-      const long long now = clock64();
-      sub[i] += (unsigned long long)(now - tm);
-      tm = now;
-    }
-  };
-  constexpr int EPL = sizeof(R) == 4 ? 16 : 8;   // entries per lane
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int k = 0; k < p; ++k) {
-    // --- left reflector on column k, rows k..r-1 (warp 0)
-    if (warp == 0) {
-      R xn2 = 0;
-      for (int i = k + 1 + lane; i < r; i += 32) xn2 += norm2(T[(size_t)k * ld + i]);
-      for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
-      Cx<R> tau, sc;
-      R beta;
-      make_reflector(T[(size_t)k * ld + k], xn2, &tau, &beta, &sc);
-      for (int i = k + 1 + lane; i < r; i += 32) {
-        const Cx<R> v = T[(size_t)k * ld + i] * sc;
-        T[(size_t)k * ld + i] = v;
-        vb[i] = v;
-      }
-      if (lane == 0) {
-        T[(size_t)k * ld + k] = cx<R>(beta, 0);
-        vb[k] = cx<R>(1, 0);
-        dd[k] = beta;
-        tauL[k] = tau;
-      }
-    }
-    __syncthreads();
-    mark(0);
-    // --- apply H^H = I - conj(tau) v v^H to columns k+1..p-1
-    {
-      const Cx<R> ct = conj(tauL[k]);
-      const int nr = r - k;
-      // lanes per column for this step: the fewest that cover the live rows
-      int lg = 0;
-      while (lg < 5 && (EPL << lg) < nr) ++lg;
-      const int LPC = 1 << lg, grp = tid >> lg, l8 = tid & (LPC - 1);
-      Cx<R> v[EPL];
+// (diagonal) and ee[k] (superdiagonal) receive the real entries, tauL/tauR the
+// reflector factors. Each step is two block-wide half steps with one barrier after
+// each: every warp recomputes the reflector from the column (left) or row (right) it
+// acts on, which that half step does not modify, so no single-warp section sits
+// between the updates. The reflector tails stay unscaled in T (left: column k below
+// the diagonal; right: row k right of the superdiagonal). Their scale factors
+// 1/(alpha - beta) are written over the consumed pivots T[k][k] (left) and
+// T[k+1][k] (right) one half step later, when no thread reads those entries.
+// Left update: 16 lanes per column, EA entries per lane (rows k + lane + 16 e).
+// Right update: G lanes per row, EB entries per lane (columns k + 1 + g + G e),
+// 32 / G consecutive rows per warp. With a leading dimension of 2 (mod 16)
+// complex<float> entries (G = 8) or an odd one for complex<double> (G = 16) both
+// walks are free of shared-memory bank conflicts.
+template <class R>
+__device__ __forceinline__ R warp_sum_norm2(const Cx<R>* x, int i0, int i1, int stride) {
+  R s = 0;
+  for (int i = i0 + (int)(threadIdx.x & 31); i < i1; i += 32) s += norm2(x[(size_t)i * stride]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <class R, int NT, int EA>
+__device__ __forceinline__ void bidiag_left_update(Cx<R>* T, int ld, int k, int r, int p, Cx<R> ct,
+                                                   Cx<R> sc) {
+  const int tid = threadIdx.x, l = tid & 15, grp = tid >> 4, wcol = (tid >> 5) << 1;
+  const int nr = r - k;
+  const Cx<R>* tk = T + (size_t)k * ld + k;
+  Cx<R> v[EA];
 #pragma unroll
-      for (int e = 0; e < EPL; ++e) {
-        const int i = k + l8 + LPC * e;
-        v[e] = (l8 + LPC * e < nr) ? vb[i] : cx<R>(0, 0);
-      }
-      for (int cbase = k + 1; cbase < p; cbase += NT / LPC) {
-        const int col = cbase + grp;
-        const bool act = col < p;
-        Cx<R>* tc = T + (size_t)(act ? col : k) * ld;
-        Cx<R> x[EPL];
-        Cx<R> s = cx<R>(0, 0);
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-          const int off = l8 + LPC * e;
-          x[e] = (act && off < nr) ? tc[k + off] : cx<R>(0, 0);
-          cmac_conj(s, v[e], x[e]);
-        }
-        for (int o = 1; o < LPC; o <<= 1) {
-          s.x += __shfl_xor_sync(0xffffffffu, s.x, o, LPC);
-          s.y += __shfl_xor_sync(0xffffffffu, s.y, o, LPC);
-        }
-        const Cx<R> f = ct * s;
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-          const int off = l8 + LPC * e;
-          if (act && off < nr) tc[k + off] = x[e] - f * v[e];
-        }
-      }
-    }
-    __syncthreads();
-    mark(1);
-    if (k >= p - 1) break;
-    // --- right reflector on row k, columns k+1..p-1 (warp 0), acting on conj(row)
-    if (warp == 0) {
-      R xn2 = 0;
-      for (int j = k + 2 + lane; j < p; j += 32) xn2 += norm2(T[(size_t)j * ld + k]);
-      for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
-      Cx<R> tau, sc;
-      R beta;
-      make_reflector(conj(T[(size_t)(k + 1) * ld + k]), xn2, &tau, &beta, &sc);
-      for (int j = k + 2 + lane; j < p; j += 32) {
-        const Cx<R> w = conj(T[(size_t)j * ld + k]) * sc;
-        T[(size_t)j * ld + k] = w;
-        wb[j] = w;
-      }
-      if (lane == 0) {
-        T[(size_t)(k + 1) * ld + k] = cx<R>(beta, 0);
-        wb[k + 1] = cx<R>(1, 0);
-        ee[k] = beta;
-        tauR[k] = tau;
-      }
-    }
-    __syncthreads();
-    mark(2);
-    // --- apply G = I - tau w w^H from the right to rows k+1..r-1, columns k+1..p-1
-    {
-      const Cx<R> t = tauR[k];
-      const int nc = p - k - 1;
-      int lg = 0;
-      while (lg < 5 && (EPL << lg) < nc) ++lg;
-      const int LPC = 1 << lg, grp = tid >> lg, l8 = tid & (LPC - 1);
-      Cx<R> w[EPL];
-#pragma unroll
-      for (int e = 0; e < EPL; ++e) {
-        const int off = l8 + LPC * e;
-        w[e] = (off < nc) ? wb[k + 1 + off] : cx<R>(0, 0);
-      }
-      for (int rbase = k + 1; rbase < r; rbase += NT / LPC) {
-        const int row = rbase + grp;
-        const bool act = row < r;
-        const int rr = act ? row : k;
-        Cx<R> x[EPL];
-        Cx<R> s = cx<R>(0, 0);
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-          const int off = l8 + LPC * e;
-          x[e] = (act && off < nc) ? T[(size_t)(k + 1 + off) * ld + rr] : cx<R>(0, 0);
-          cmac(s, x[e], w[e]);
-        }
-        for (int o = 1; o < LPC; o <<= 1) {
-          s.x += __shfl_xor_sync(0xffffffffu, s.x, o, LPC);
-          s.y += __shfl_xor_sync(0xffffffffu, s.y, o, LPC);
-        }
-        const Cx<R> f = t * s;
-#pragma unroll
-        for (int e = 0; e < EPL; ++e) {
-          const int off = l8 + LPC * e;
-          if (act && off < nc) T[(size_t)(k + 1 + off) * ld + rr] = x[e] - f * conj(w[e]);
-        }
-      }
-    }
-    __syncthreads();
-    mark(3);
+  for (int e = 0; e < EA; ++e) {
+    const int off = l + 16 * e;
+    v[e] = off == 0 ? cx<R>(1, 0) : (off < nr ? tk[off] * sc : cx<R>(0, 0));
   }
+  // the loop test is uniform over a warp (its two columns are cbase + wcol, + 1)
+  for (int cbase = k + 1; cbase + wcol < p; cbase += NT / 16) {
+    const int col = cbase + grp;
+    const bool act = col < p;
+    Cx<R>* tc = T + (size_t)(act ? col : k) * ld + k;
+    Cx<R> x[EA];
+    Cx<R> s = cx<R>(0, 0);
+#pragma unroll
+    for (int e = 0; e < EA; ++e) {
+      const int off = l + 16 * e;
+      x[e] = (act && off < nr) ? tc[off] : cx<R>(0, 0);
+      cmac_conj(s, v[e], x[e]);
+    }
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, o, 16);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, o, 16);
+    }
+    const Cx<R> f = ct * s;
+#pragma unroll
+    for (int e = 0; e < EA; ++e) {
+      const int off = l + 16 * e;
+      if (act && off < nr) tc[off] = x[e] - f * v[e];
+    }
+  }
+}
+
+template <class R, int NT, int G, int EB>
+__device__ __forceinline__ void bidiag_right_update(Cx<R>* T, int ld, int k, int r, int p, Cx<R> t,
+                                                    Cx<R> sc) {
+  const int tid = threadIdx.x, g = tid & (G - 1), rw = tid / G, wrow = (tid >> 5) * (32 / G);
+  const int nc = p - k - 1;
+  Cx<R> w[EB];
+#pragma unroll
+  for (int e = 0; e < EB; ++e) {
+    const int off = g + G * e;
+    w[e] = off == 0 ? cx<R>(1, 0)
+                    : (off < nc ? conj(T[(size_t)(k + 1 + off) * ld + k]) * sc : cx<R>(0, 0));
+  }
+  Cx<R>* t1 = T + (size_t)(k + 1) * ld;
+  for (int rbase = k + 1; rbase + wrow < r; rbase += NT / G) {
+    const int row = rbase + rw;
+    const bool act = row < r;
+    Cx<R> x[EB];
+    Cx<R> s = cx<R>(0, 0);
+#pragma unroll
+    for (int e = 0; e < EB; ++e) {
+      const int off = g + G * e;
+      x[e] = (act && off < nc) ? t1[(size_t)off * ld + row] : cx<R>(0, 0);
+      cmac(s, x[e], w[e]);
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      s.x += __shfl_xor_sync(0xffffffffu, s.x, o, G);
+      s.y += __shfl_xor_sync(0xffffffffu, s.y, o, G);
+    }
+    const Cx<R> f = t * s;
+#pragma unroll
+    for (int e = 0; e < EB; ++e) {
+      const int off = g + G * e;
+      if (act && off < nc) t1[(size_t)off * ld + row] = x[e] - f * conj(w[e]);
+    }
+  }
+}
+
+// r <= 256 rows, p <= r columns.
+template <class R, int NT>
+__device__ void bidiagonalize(Cx<R>* T, int ld, int r, int p, R* dd, R* ee, Cx<R>* tauL, Cx<R>* tauR) {
+  Cx<R> pend_r = cx<R>(0, 0);   // thread 0: scale of the last right reflector
+  for (int k = 0; k < p; ++k) {
+    // --- left half step: reflector of column k (rows k..r-1), applied to columns k+1..p-1
+    Cx<R>* ck = T + (size_t)k * ld;
+    Cx<R> tau, sc;
+    R beta;
+    make_reflector(ck[k], warp_sum_norm2(ck, k + 1, r, 1), &tau, &beta, &sc);
+    if (threadIdx.x == 0) {
+      dd[k] = beta;
+      tauL[k] = tau;
+      if (k > 0) ck[k - 1] = pend_r;   // T[k][k-1]: pivot of right reflector k-1
+    }
+    const Cx<R> sc_l = sc;
+    if (k + 1 < p) {
+      const int nr = r - k;
+      const Cx<R> ct = conj(tau);
+      if (nr <= 16) bidiag_left_update<R, NT, 1>(T, ld, k, r, p, ct, sc);
+      else if (nr <= 32) bidiag_left_update<R, NT, 2>(T, ld, k, r, p, ct, sc);
+      else if (nr <= 64) bidiag_left_update<R, NT, 4>(T, ld, k, r, p, ct, sc);
+      else if (nr <= 128) bidiag_left_update<R, NT, 8>(T, ld, k, r, p, ct, sc);
+      else bidiag_left_update<R, NT, 16>(T, ld, k, r, p, ct, sc);
+    }
+    __syncthreads();
+    if (k + 1 >= p) {
+      if (threadIdx.x == 0) ck[k] = sc_l;
+      break;
+    }
+    // --- right half step: reflector of conj(row k) (columns k+1..p-1), applied to
+    //     rows k+1..r-1
+    make_reflector(conj(T[(size_t)(k + 1) * ld + k]), warp_sum_norm2(T + k, k + 2, p, ld), &tau, &beta,
+                   &sc);
+    if (threadIdx.x == 0) {
+      ee[k] = beta;
+      tauR[k] = tau;
+      ck[k] = sc_l;   // T[k][k]: pivot of left reflector k
+      pend_r = sc;
+    }
+    {
+      // 8 lanes per row for complex<float>, 16 for complex<double> (register budget)
+      constexpr int G = sizeof(R) == 4 ? 8 : 16;
+      const int nc = p - k - 1;
+      if (nc <= G) bidiag_right_update<R, NT, G, 1>(T, ld, k, r, p, tau, sc);
+      else if (nc <= 2 * G) bidiag_right_update<R, NT, G, 2>(T, ld, k, r, p, tau, sc);
+      else if (nc <= 4 * G) bidiag_right_update<R, NT, G, 4>(T, ld, k, r, p, tau, sc);
+      else if (nc <= 8 * G) bidiag_right_update<R, NT, G, 8>(T, ld, k, r, p, tau, sc);
+      else if (nc <= 16 * G) bidiag_right_update<R, NT, G, 16>(T, ld, k, r, p, tau, sc);
+      else bidiag_right_update<R, NT, 16, 16>(T, ld, k, r, p, tau, sc);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
 }
 
 // Number of singular values of B that are >= x, from the negative count of the
@@ -357,165 +365,103 @@ __device__ void owning_block(const R* b2, int N, const R* sig, int t, R delta, R
   }
 }
 
-// Cholesky-QR twice over the rows of W (k x p, row stride ldw): G = W W^T, G = L L^T,
-// W <- L^{-1} W. Row t of the result depends only on rows 0..t (Gram-Schmidt order),
-// so the leading singular vectors are kept as computed. A pivot below 1e-6 of its
+// Block classical Gram-Schmidt twice (BCGS2) over the rows of W (k x p, row stride
+// ldw), in blocks of 8 rows. Each of the two repetitions projects the block out of all
+// earlier rows and then orthonormalises it internally by Cholesky QR (G = W_b W_b^T =
+// L L^T, W_b <- L^{-1} W_b). Row t of the result depends only on rows 0..t, so the
+// leading singular vectors keep their directions. A Cholesky pivot below 1e-6 of its
 // diagonal (a row that is numerically a combination of earlier rows) counts as a
-// collapse. G: k x k shared scratch.
+// collapse. coef: >= 8 k shared scratch (used once k > 8); small: >= 128 shared.
 template <class R, int NT>
-__device__ void orthonormalize_rows_chol(R* W, int ldw, int k, int p, R* G, int* collapsed) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int pass = 0; pass < 2; ++pass) {
-    // G = W W^T (lower triangle)
-    for (int e = tid; e < k * k; e += NT) {
-      const int a = e / k, b = e - a * k;
-      if (b > a) continue;
-      R acc = 0;
-      const R* wa = W + (size_t)a * ldw;
-      const R* wb = W + (size_t)b * ldw;
-#pragma unroll 4
-      for (int q = 0; q < p; ++q) acc += wa[q] * wb[q];
-      G[a * k + b] = acc;
-    }
-    __syncthreads();
-    // in-place Cholesky (lower), one warp
-    if (warp == 0) {
-      for (int j = 0; j < k; ++j) {
-        R d = G[j * k + j];
-        for (int u = lane; u < j; u += 32) {
-          const R l = G[j * k + u];
-          d -= l * l;  // partial, reduced below
-        }
-        // reduce the partial subtraction across lanes
-        R part = G[j * k + j] - d;
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        const R diag = G[j * k + j];
-        R piv = diag - part;
-        if (lane == 0 && !(piv > R(1e-6) * diag)) {
-          ++*collapsed;
-        }
-        if (!(piv > R(0))) piv = diag > R(0) ? diag * R(1e-30) : R(1e-30);
-        const R ljj = sqrt(piv);
-        __syncwarp();
-        for (int i = j + 1 + lane; i < k; i += 32) {
-          R v = G[i * k + j];
-          for (int u = 0; u < j; ++u) v -= G[i * k + u] * G[j * k + u];
-          G[i * k + j] = v / ljj;
-        }
-        __syncwarp();
-        if (lane == 0) G[j * k + j] = ljj;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    // W <- L^{-1} W, one thread per column
-    for (int q = tid; q < p; q += NT) {
-      for (int t = 0; t < k; ++t) {
-        R v = W[(size_t)t * ldw + q];
-        for (int u = 0; u < t; ++u) v -= G[t * k + u] * W[(size_t)u * ldw + q];
-        W[(size_t)t * ldw + q] = v / G[t * k + t];
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Block classical Gram-Schmidt (twice) over the rows of W (k x p, row stride ldw), in
-// blocks of 8 rows: each block is projected out of all earlier rows in two passes, then
-// orthonormalised internally by one warp (modified Gram-Schmidt). Row t of the result
-// depends only on rows 0..t, so the leading singular vectors keep their directions. A
-// row whose remainder falls below 1e-3 of its norm counts as a collapse.
-// coef: >= 8 k shared scratch.
-template <class R, int NT>
-__device__ void orthonormalize_rows_block(R* W, int ldw, int k, int p, R* coef, int* collapsed) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ void orthonormalize_rows_block(R* W, int ldw, int k, int p, R* coef, R* small, int* collapsed) {
+  const int tid = threadIdx.x;
   for (int b0 = 0; b0 < k; b0 += 8) {
     const int nb = min(8, k - b0);
-    for (int pass = 0; pass < 2 && b0 > 0; ++pass) {
-      // coef[u * 8 + j] = <w_u, w_{b0+j}>, 8 lanes per dot
-      const int nd = b0 * nb;
-      for (int base = 0; base < nd * 8; base += NT) {
+    for (int rep = 0; rep < 2; ++rep) {
+      if (b0 > 0) {
+        // coef[u * 8 + j] = <w_u, w_{b0+j}>, 8 lanes per dot
+        const int nd = b0 * nb;
+        for (int base = 0; base < nd * 8; base += NT) {
+          const int d = (base + tid) >> 3, l = tid & 7;
+          const bool act = d < nd;
+          const int u = act ? d / nb : 0, j = act ? d - u * nb : 0;
+          R acc = 0;
+          if (act)
+            for (int q = l; q < p; q += 8) acc += W[(size_t)u * ldw + q] * W[(size_t)(b0 + j) * ldw + q];
+          for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (act && l == 0) coef[u * 8 + j] = acc;
+        }
+        __syncthreads();
+        for (int it = tid; it < nb * p; it += NT) {
+          const int j = it / p, q = it - j * p;
+          R v = W[(size_t)(b0 + j) * ldw + q];
+          for (int u = 0; u < b0; ++u) v -= coef[u * 8 + j] * W[(size_t)u * ldw + q];
+          W[(size_t)(b0 + j) * ldw + q] = v;
+        }
+        __syncthreads();
+      }
+      // Gram matrix of the block (lower triangle): small[i * 8 + j], j <= i
+      const int ng = nb * (nb + 1) / 2;
+      for (int base = 0; base < ng * 8; base += NT) {
         const int d = (base + tid) >> 3, l = tid & 7;
-        const bool act = d < nd;
-        const int u = act ? d / nb : 0, j = act ? d - u * nb : 0;
+        const bool act = d < ng;
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= d && i < 7) ++i;
+        const int j = d - i * (i + 1) / 2;
         R acc = 0;
         if (act)
-          for (int q = l; q < p; q += 8) acc += W[(size_t)u * ldw + q] * W[(size_t)(b0 + j) * ldw + q];
+          for (int q = l; q < p; q += 8) acc += W[(size_t)(b0 + i) * ldw + q] * W[(size_t)(b0 + j) * ldw + q];
         for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (act && l == 0) coef[u * 8 + j] = acc;
+        if (act && l == 0) small[i * 8 + j] = acc;
       }
       __syncthreads();
-      for (int it = tid; it < nb * p; it += NT) {
-        const int j = it / p, q = it - j * p;
-        R v = W[(size_t)(b0 + j) * ldw + q];
-        for (int u = 0; u < b0; ++u) v -= coef[u * 8 + j] * W[(size_t)u * ldw + q];
-        W[(size_t)(b0 + j) * ldw + q] = v;
-      }
-      __syncthreads();
-    }
-    if (warp == 0) {
-      for (int j = 0; j < nb; ++j) {
-        R* wj = W + (size_t)(b0 + j) * ldw;
-        R n0 = 0;
-        for (int q = lane; q < p; q += 32) n0 += wj[q] * wj[q];
-        for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(0xffffffffu, n0, o);
-        for (int rep = 0; rep < 2; ++rep)
-          for (int i = 0; i < j; ++i) {
-            const R* wi = W + (size_t)(b0 + i) * ldw;
-            R d = 0;
-            for (int q = lane; q < p; q += 32) d += wi[q] * wj[q];
-            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-            for (int q = lane; q < p; q += 32) wj[q] -= d * wi[q];
-            __syncwarp();
+      // Cholesky factor L (in place) and its inverse X = L^{-1} at small + 64; one thread
+      if (tid == 0) {
+        R* G = small;
+        R* X = small + 64;
+        for (int j = 0; j < nb; ++j) {
+          const R gjj = G[j * 8 + j];
+          R d = gjj;
+          for (int u = 0; u < j; ++u) d -= G[j * 8 + u] * G[j * 8 + u];
+          if (!(d > R(1e-6) * gjj)) {
+            ++*collapsed;
+            d = gjj > R(0) ? gjj * R(1e-30) : R(1e-30);
           }
-        R nr = 0;
-        for (int q = lane; q < p; q += 32) nr += wj[q] * wj[q];
-        for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
-        if (lane == 0 && !(nr > R(1e-6) * n0)) ++*collapsed;
-        const R inv = nr > R(0) ? R(1) / sqrt(nr) : R(0);
-        for (int q = lane; q < p; q += 32) wj[q] *= inv;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Classical Gram-Schmidt twice over the rows of W (k x p, row stride ldw), in order.
-template <class R, int NT>
-__device__ void orthonormalize_rows(R* W, int ldw, int k, int p, R* coef, int* collapsed) {
-  const int tid = threadIdx.x;
-  for (int t = 0; t < k; ++t) {
-    for (int pass = 0; pass < 2; ++pass) {
-      // coef[s] = <w_s, w_t> for s < t, 8 threads per dot
-      const int s = tid >> 3, l8 = tid & 7;
-      for (int sb = s; ; sb += NT / 8) {
-        const bool act = sb < t;
-        if (!__any_sync(0xffffffffu, act)) break;
-        R acc = 0;
-        if (act)
-          for (int q = l8; q < p; q += 8) acc += W[(size_t)sb * ldw + q] * W[(size_t)t * ldw + q];
-        for (int o = 1; o < 8; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (act && l8 == 0) coef[sb] = acc;
+          const R ljj = sqrt(d);
+          G[j * 8 + j] = ljj;
+          for (int i = j + 1; i < nb; ++i) {
+            R v = G[i * 8 + j];
+            for (int u = 0; u < j; ++u) v -= G[i * 8 + u] * G[j * 8 + u];
+            G[i * 8 + j] = v / ljj;
+          }
+        }
+        for (int j = 0; j < nb; ++j) {
+          X[j * 8 + j] = R(1) / G[j * 8 + j];
+          for (int i = j + 1; i < nb; ++i) {
+            R v = 0;
+            for (int u = j; u < i; ++u) v += G[i * 8 + u] * X[u * 8 + j];
+            X[i * 8 + j] = -v / G[i * 8 + i];
+          }
+        }
       }
       __syncthreads();
+      // W_b <- X W_b, one thread per column
       for (int q = tid; q < p; q += NT) {
-        R v = W[(size_t)t * ldw + q];
-        for (int u = 0; u < t; ++u) v -= coef[u] * W[(size_t)u * ldw + q];
-        W[(size_t)t * ldw + q] = v;
+        R x[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = i < nb ? W[(size_t)(b0 + i) * ldw + q] : R(0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          if (i < nb) {
+            R y = 0;
+#pragma unroll
+            for (int u = 0; u <= i; ++u) y += small[64 + i * 8 + u] * x[u];
+            W[(size_t)(b0 + i) * ldw + q] = y;
+          }
+        }
       }
       __syncthreads();
     }
-    // normalise row t (warp 0)
-    if ((tid >> 5) == 0) {
-      R acc = 0;
-      for (int q = tid; q < p; q += 32) acc += W[(size_t)t * ldw + q] * W[(size_t)t * ldw + q];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      const R inv = acc > R(0) ? R(1) / sqrt(acc) : R(0);
-      if (tid == 0 && acc < R(1e-6)) ++*collapsed;
-      for (int q = tid; q < p; q += 32) W[(size_t)t * ldw + q] *= inv;
-    }
-    __syncthreads();
   }
 }
 

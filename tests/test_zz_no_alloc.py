@@ -16,7 +16,17 @@ from paper_2207_03711_gb300 import synthetic as syn
 
 pytestmark = pytest.mark.gpu
 
-LAM_TOL, BLK_TOL = 2e-5, 2e-4
+LAM_TOL, INFIDELITY_TOL = 2e-5, 1e-6
+
+
+def overlap(xs, ys):
+    """<x|y> of two MPS given as site tensors (r_{k-1}, 2, r_k), left to right."""
+    e = np.ones((1, 1), dtype=np.complex128)
+    for x, y in zip(xs, ys):
+        x = x.astype(np.complex128)
+        y = y.astype(np.complex128)
+        e = np.einsum("ab,asc,bsd->cd", e, x.conj(), y)
+    return e[0, 0]
 
 
 def caps(n, chi):
@@ -79,13 +89,12 @@ def test_noalloc_matches_allocating_path():
         full = [1] + list(rk) + [1]
         for q in range(n - 1):
             assert np.abs(lm[q, :full[q + 1]] - lams_ref[q]).max() <= LAM_TOL
-        for q in range(1, n - 1):
-            Bq = fl[off[q]:off[q] + full[q] * 2 * full[q + 1]].reshape(full[q], 2, full[q + 1])
-            Bq1 = fl[off[q + 1]:off[q + 1] + full[q + 1] * 2 * full[q + 2]].reshape(full[q + 1], 2, full[q + 2])
-            ll = lams_ref[q - 1]
-            blk = ll[:, None, None, None] * np.einsum("aib,bjc->aijc", Bq, Bq1)
-            ref = ll[:, None, None, None] * np.einsum("aib,bjc->aijc", sites_ref[q], sites_ref[q + 1])
-            assert np.linalg.norm(blk - ref) <= BLK_TOL * np.linalg.norm(ref)
+        # site tensors carry the gauge of every bond (singular-vector phases are not
+        # unique), so the states are compared through their overlap
+        sites = [fl[off[q]:off[q] + full[q] * 2 * full[q + 1]].reshape(full[q], 2, full[q + 1])
+                 for q in range(n)]
+        ab, aa, bb = overlap(sites, sites_ref), overlap(sites, sites), overlap(sites_ref, sites_ref)
+        assert 1.0 - abs(ab) / np.sqrt(abs(aa) * abs(bb)) <= INFIDELITY_TOL
 
 
 def test_noalloc_rejects_sizes_beyond_the_workspace():
