@@ -163,9 +163,17 @@ int vqe_energy(mps_t mps, circ_t circ, ham_t ham, const double* theta, double* e
 int vqe_energy_batch(mps_t mps, circ_t circ, ham_t ham, int n_batch, const double* thetas,
                      double* energies);
 
-/* Parameter-shift gradient dE/dtheta_e for the n_sel parameters sel[]:
- * sum over the rotations k of e of scale_k [E(phi_k + pi/2) - E(phi_k - pi/2)] / 2,
- * all shifted circuits batched over slots (needs n_slots >= 2). */
+/* Parameter-shift gradient dE/dtheta_e for the n_sel parameters sel[] (not in the
+ * paper, which optimises with energies only; the rule is exact for rotations
+ * exp(-i phi P / 2)): sum over the rotations k of e of
+ * scale_k [E(phi_k + pi/2) - E(phi_k - pi/2)] / 2.
+ * With n_slots >= 3 the shifted circuits share prefixes: slot 0 carries the unshifted
+ * circuit up to rotation k's parametric gate, where its state is copied to two slots
+ * that continue with phi_k +- pi/2; up to (n_slots - 1) / 2 rotations run together in
+ * one batched pass. With fewer slots each shifted circuit runs from the reference
+ * state in slot 0. Both routes do the same arithmetic per gate, so they agree bit for
+ * bit. The contents of every slot are overwritten. Returns MPS_ENOCONV if any
+ * evaluation hit the Jacobi sweep cap (grad is still written). */
 int vqe_gradient(mps_t mps, circ_t circ, ham_t ham, const double* theta, int n_sel,
                  const int32_t* sel, double* grad);
 
@@ -190,6 +198,13 @@ typedef struct {
                            /* SVD with right vectors + site update)                */
 } mps_stats_t;
 int mps_get_stats(mps_t mps, mps_stats_t* stats);
+
+/* Device bytes that a handle of these sizes would hold once it has run circ (null:
+ * circuit buffers left out) and measured ham (null: measurement buffers left out).
+ * No paper counterpart: serving loops use it to admit requests by device memory. The
+ * figure counts the handle's own buffers (within a few KB), not allocator rounding. */
+int mps_estimate_bytes(int n_qubits, int chi, int precision, int n_slots, circ_t circ, ham_t ham,
+                       size_t* bytes);
 
 int mps_destroy(mps_t mps);
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "vqe_gradient": [_P, _P, _P, _P, _I, _P, _P],
     "mps_get_stats": [_P, ctypes.POINTER(MpsStats)],
     "mps_destroy": [_P],
+    "mps_estimate_bytes": [_I, _I, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_size_t)],
     "mps_apply_gates_noalloc": [_I, _I, _P, _P, _P, _P, _I64, _P, _P, _P, _PD],
     "mps_last_error": [],
 }
@@ -339,10 +340,11 @@ def vqe_energy_batch(mps, circ, ham, thetas, allow_noconv=True):
     return out
 
 
-def vqe_gradient(mps, circ, ham, theta, sel):
+def vqe_gradient(mps, circ, ham, theta, sel, allow_noconv=True):
     sel = np.ascontiguousarray(sel, dtype=np.int32)
     out = np.zeros(sel.shape[0])
-    _check(load_library().vqe_gradient(mps, circ, ham, _ptr(_f64(theta)), sel.shape[0], _ptr(sel), _ptr(out)))
+    _check(load_library().vqe_gradient(mps, circ, ham, _ptr(_f64(theta)), sel.shape[0], _ptr(sel), _ptr(out)),
+           allow=(MPS_ENOCONV,) if allow_noconv else ())
     return out
 
 
@@ -364,6 +366,12 @@ def mps_get_stats(mps):
     out = {k: getattr(s, k) for k, _ in MpsStats._fields_}
     out["cycles"] = list(s.cycles)
     return out
+
+
+def mps_estimate_bytes(n_qubits, chi, precision=MPS_FP64, n_slots=1, circ=None, ham=None):
+    out = ctypes.c_size_t(0)
+    _check(load_library().mps_estimate_bytes(n_qubits, chi, precision, n_slots, circ, ham, ctypes.byref(out)))
+    return int(out.value)
 
 
 def mps_last_error():

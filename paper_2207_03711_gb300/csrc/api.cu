@@ -105,6 +105,7 @@ struct mps_s {
   double* d_theta = nullptr;
   size_t theta_cap = 0;
   uint8_t* d_occ = nullptr;
+  int64_t* d_start_gate = nullptr;
   int64_t* d_shift_gate = nullptr;
   double* d_shift_val = nullptr;
   double cutoff = 1e-13;
@@ -132,6 +133,7 @@ struct mps_s {
     dfree(w.out);
     dfree(d_theta);
     dfree(d_occ);
+    dfree(d_start_gate);
     dfree(d_shift_gate);
     dfree(d_shift_val);
     for (auto e : ev)
@@ -272,21 +274,37 @@ static int ensure_meas(mps_s* m, int32_t nodes, int64_t terms) {
 
 // Apply gates [0, n_gates) of circ to slots [slot0, slot0 + count); thetas: count x n_params
 // (host). shifts: optional per-slot (gate index, extra angle) for parameter shifts.
+// Apply the circuit to slots [slot0, slot0 + count) with per-slot parameters thetas
+// ([count][n_params], host; null keeps the device copy). Optional per-slot host arrays:
+// start (first gate), shift_gate / shift_phi (angle shift of one parametric gate).
+// Gates [min start, g_end) are launched; g_end < 0 means the whole list.
 static int run_circuit(mps_s* m, circ_s* c, int slot0, int count, const double* thetas,
-                       const int64_t* shift_gate, const double* shift_val) {
+                       const int64_t* start = nullptr, const int64_t* shift_gate = nullptr,
+                       const double* shift_phi = nullptr, int64_t g_end = -1) {
   TRY(upload_circ(c));
   const int np = std::max(1, c->comp.n_params);
   TRY(ensure_theta(m, (size_t)count * np));
   if (thetas && c->comp.n_params > 0)
     CU(cudaMemcpyAsync(m->d_theta, thetas, (size_t)count * np * 8, cudaMemcpyHostToDevice, m->st));
-  (void)shift_gate;
-  (void)shift_val;
   CircDev cd{c->d_gates, (int64_t)c->comp.gates.size(), c->d_mats, np};
-  const int64_t G = (int64_t)c->comp.gates.size();
+  const int64_t G = g_end < 0 ? (int64_t)c->comp.gates.size() : std::min<int64_t>(g_end, c->comp.gates.size());
+  int64_t g_begin = 0;
+  if (start) {
+    g_begin = G;
+    for (int b = 0; b < count; ++b) g_begin = std::min(g_begin, start[b]);
+    CU(cudaMemcpyAsync(m->d_start_gate, start, (size_t)count * 8, cudaMemcpyHostToDevice, m->st));
+    cd.start_gate = m->d_start_gate;
+  }
+  if (shift_gate && shift_phi) {
+    CU(cudaMemcpyAsync(m->d_shift_gate, shift_gate, (size_t)count * 8, cudaMemcpyHostToDevice, m->st));
+    CU(cudaMemcpyAsync(m->d_shift_val, shift_phi, (size_t)count * 8, cudaMemcpyHostToDevice, m->st));
+    cd.shift_gate = m->d_shift_gate;
+    cd.shift_phi = m->d_shift_val;
+  }
   const int64_t chunk = 16384;
   CU(cudaEventRecord(m->ev[0], m->st));
   int launches = 0;
-  for (int64_t g0 = 0; g0 < G; g0 += chunk) {
+  for (int64_t g0 = g_begin; g0 < G; g0 += chunk) {
     CU(launch_circuit(m->dm, m->prec, cd, g0, std::min(G, g0 + chunk), slot0, count, m->d_theta, m->cutoff,
                       m->max_sweeps, m->st));
     ++launches;
@@ -297,7 +315,20 @@ static int run_circuit(mps_s* m, circ_s* c, int slot0, int count, const double* 
   CU(cudaEventElapsedTime(&ms, m->ev[0], m->ev[1]));
   m->stats.ms_circuit += ms;
   m->stats.kernel_launches += launches;
-  m->stats.n_gates = G;
+  m->stats.n_gates = (int64_t)c->comp.gates.size();
+  return MPS_OK;
+}
+
+// Copy the whole state of slot src (tensors, ranks, lambda, accumulators) to slot dst.
+static int copy_slot(mps_s* m, int src, int dst) {
+  const size_t sb = (size_t)m->dm.slot_elems * m->es;
+  CU(cudaMemcpyAsync((char*)m->dm.B + dst * sb, (char*)m->dm.B + src * sb, sb, cudaMemcpyDeviceToDevice, m->st));
+  const size_t nl = (size_t)(m->n - 1) * m->chi;
+  CU(cudaMemcpyAsync(m->dm.lam + dst * nl, m->dm.lam + src * nl, nl * 8, cudaMemcpyDeviceToDevice, m->st));
+  const size_t nr = (size_t)m->n + 1;
+  CU(cudaMemcpyAsync(m->dm.rank + dst * nr, m->dm.rank + src * nr, nr * 4, cudaMemcpyDeviceToDevice, m->st));
+  CU(cudaMemcpyAsync(m->dm.dw + dst, m->dm.dw + src, 8, cudaMemcpyDeviceToDevice, m->st));
+  CU(cudaMemcpyAsync(m->dm.stat + 4 * dst, m->dm.stat + 4 * src, 16, cudaMemcpyDeviceToDevice, m->st));
   return MPS_OK;
 }
 
@@ -483,6 +514,38 @@ int circ_destroy(circ_t c) {
   return MPS_OK;
 }
 
+int mps_estimate_bytes(int n_qubits, int chi, int precision, int n_slots, circ_t circ, ham_t ham,
+                       size_t* bytes) {
+  if (!bytes) return fail(MPS_EINVAL, "mps_estimate_bytes: null pointer");
+  if (n_qubits < 2 || n_qubits > kMaxQubits || chi < 1 || chi > 128 || n_slots < 1 ||
+      (precision != MPS_FP64 && precision != MPS_MIXED))
+    return fail(MPS_EINVAL, "mps_estimate_bytes: bad sizes");
+  const int n = n_qubits;
+  const size_t es = precision == MPS_FP64 ? 16 : 8, S = (size_t)n_slots, mm = 2 * (size_t)chi;
+  std::vector<int64_t> cap(n + 1, 1);
+  for (int b = 0; b < n - 1; ++b) {
+    const int e = std::min(b + 1, n - 1 - b);
+    cap[b + 1] = e >= 30 ? chi : std::min(chi, 1 << e);
+  }
+  size_t slot = 0;
+  for (int k = 0; k < n; ++k) slot += (size_t)cap[k] * 2 * cap[k + 1];
+  size_t b = S * slot * es                          // site tensors
+             + S * (n - 1) * chi * 8 + S * (n + 1) * 4  // lambda, ranks
+             + S * mm * mm * es + S * mm * (mm + 16) * es + S * 16 * chi * chi * 8  // workspaces
+             + S * (8 + 16 + 64 + n + 24) + (size_t)n * 8;
+  const size_t chi2 = (size_t)chi * chi;
+  b += (size_t)(n + 1) * chi2 * es + slot * es;     // right environments, B-hat
+  if (circ) b += circ->comp.gates.size() * sizeof(GateRec) + circ->comp.mats.size() * 16 +
+                 S * std::max(1, circ->comp.n_params) * 8;
+  if (ham) {
+    const size_t T = ham->terms.size(), nodes = std::max<int32_t>(1, ham->trie.max_level_nodes);
+    b += 4 * nodes * chi2 * es + (4 + 4 * T) * 8;   // L (two levels), T, values
+    b += T * (8 + 4 + 1 + 4) + T * (size_t)n;       // coefficients and the trie arrays
+  }
+  *bytes = b;
+  return MPS_OK;
+}
+
 int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_stream, mps_t* out) {
   if (!out) return fail(MPS_EINVAL, "mps_create: null pointer");
   if (n_qubits < 2 || n_qubits > kMaxQubits) return fail(MPS_EINVAL, "mps_create: n_qubits out of [2, 128]");
@@ -534,6 +597,7 @@ int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_str
   CU(cudaMemcpy(m->d_site_off, m->site_off.data(), n * 8, cudaMemcpyHostToDevice));
   d.site_off = m->d_site_off;
   TRY(dalloc(&m->d_occ, (size_t)n_slots * n));
+  TRY(dalloc(&m->d_start_gate, n_slots));
   TRY(dalloc(&m->d_shift_gate, n_slots));
   TRY(dalloc(&m->d_shift_val, n_slots));
   for (auto& e : m->ev) CU(cudaEventCreate(&e));
@@ -597,7 +661,7 @@ int mps_apply_circuit(mps_t m, circ_t c, const double* theta, double* discarded_
   // the discarded-weight accumulator and stats of slot 0 restart at this call
   CU(cudaMemsetAsync(m->dm.dw, 0, 8, m->st));
   CU(cudaMemsetAsync(m->dm.stat, 0, 16, m->st));
-  TRY(run_circuit(m, c, 0, 1, theta, nullptr, nullptr));
+  TRY(run_circuit(m, c, 0, 1, theta));
   return finish_apply(m, discarded_weight);
 }
 
@@ -620,7 +684,7 @@ int mps_apply_gates(mps_t m, int64_t n_gates, const int32_t* bond, const double*
   reset_stats(m);
   CU(cudaMemsetAsync(m->dm.dw, 0, 8, m->st));
   CU(cudaMemsetAsync(m->dm.stat, 0, 16, m->st));
-  TRY(run_circuit(m, &c, 0, 1, nullptr, nullptr, nullptr));
+  TRY(run_circuit(m, &c, 0, 1, nullptr));
   return finish_apply(m, discarded_weight);
 }
 
@@ -762,7 +826,7 @@ int vqe_energy_batch(mps_t m, circ_t c, ham_t h, int n_batch, const double* thet
   std::vector<uint8_t> occ((size_t)n_batch * m->n);
   for (int b = 0; b < n_batch; ++b) std::memcpy(&occ[(size_t)b * m->n], c->comp.reference.data(), m->n);
   TRY(upload_reset(m, 0, n_batch, occ.data()));
-  TRY(run_circuit(m, c, 0, n_batch, thetas, nullptr, nullptr));
+  TRY(run_circuit(m, c, 0, n_batch, thetas));
   int rc = finish_apply(m, nullptr);
   if (rc != MPS_OK && rc != MPS_ENOCONV) return rc;
   m->h_out.resize(4 + 2 * h->terms.size());
@@ -775,33 +839,108 @@ int vqe_energy_batch(mps_t m, circ_t c, ham_t h, int n_batch, const double* thet
 
 int vqe_gradient(mps_t m, circ_t c, ham_t h, const double* theta, int n_sel, const int32_t* sel, double* grad) {
   if (!m || !c || !h || !theta || !sel || !grad) return fail(MPS_EINVAL, "vqe_gradient: null pointer");
+  if (c->comp.n != m->n || h->n != m->n) return fail(MPS_EINVAL, "vqe_gradient: qubit count mismatch");
   const int np = c->comp.n_params;
   for (int i = 0; i < n_sel; ++i)
     if (sel[i] < 0 || sel[i] >= np) return fail(MPS_EINVAL, "vqe_gradient: parameter index out of range");
   // Each rotation k of parameter e contributes scale_k [E(phi_k + pi/2) - E(phi_k - pi/2)] / 2.
-  // A shift of rotation k alone is applied by a fixed-angle copy of the circuit.
+  // The two shifted circuits of rotation k differ from the unshifted one first at k's
+  // parametric gate p_k, so they start from a copy of the unshifted state at p_k.
+  struct Target {
+    int sel_i;
+    int64_t gate;
+    double scale;
+  };
   const auto& R = c->comp.rotations;
-  for (int i = 0; i < n_sel; ++i) {
-    double g = 0.0;
-    for (size_t k = 0; k < R.size(); ++k) {
-      if (R[k].param != sel[i]) continue;
+  const auto& Gs = c->comp.gates;
+  std::vector<Target> tg;
+  for (size_t k = 0; k < R.size(); ++k) {
+    if (R[k].param < 0) continue;
+    int si = -1;
+    for (int i = 0; i < n_sel; ++i)
+      if (sel[i] == R[k].param) si = i;
+    if (si < 0) continue;
+    const int64_t g1 = k + 1 < R.size() ? c->comp.rot_first_gate[k + 1] : (int64_t)Gs.size();
+    int64_t pk = -1;
+    for (int64_t g = c->comp.rot_first_gate[k]; g < g1; ++g)
+      if (Gs[g].param >= 0) {
+        pk = g;
+        break;
+      }
+    if (pk < 0) return fail(MPS_EINVAL, "vqe_gradient: rotation without a parametric gate");
+    tg.push_back({si, pk, R[k].scale});
+  }
+  for (int i = 0; i < n_sel; ++i) grad[i] = 0.0;
+  reset_stats(m);
+  const int64_t G = (int64_t)Gs.size();
+  const std::vector<uint8_t>& ref = c->comp.reference;
+  m->h_out.resize(4 + 2 * h->terms.size());
+  int rc_all = MPS_OK;
+  auto keep = [&](int rc) {
+    if (rc == MPS_ENOCONV) rc_all = MPS_ENOCONV;
+    return rc == MPS_OK || rc == MPS_ENOCONV;
+  };
+  if (m->n_slots < 3) {
+    // one slot: every shifted circuit from the reference state
+    for (const Target& t : tg) {
       double e2[2];
       for (int sgn = 0; sgn < 2; ++sgn) {
-        std::vector<Rotation> rots = R;
-        rots[k].param = -1;
-        rots[k].scale = R[k].scale * theta[R[k].param] + (sgn == 0 ? kHalfPi : -kHalfPi);
-        circ_t cs = nullptr;
-        TRY(finish_circ(c->comp.n, rots, np, &cs));
-        std::unique_ptr<circ_s> hold(cs);
-        cs->comp.reference = c->comp.reference;
-        int rc = vqe_energy(m, cs, h, theta, &e2[sgn]);
-        if (rc != MPS_OK && rc != MPS_ENOCONV) return rc;
+        const int64_t zero = 0, sg = t.gate;
+        const double ph = sgn == 0 ? kHalfPi : -kHalfPi;
+        TRY(upload_reset(m, 0, 1, ref.data()));
+        TRY(run_circuit(m, c, 0, 1, theta, &zero, &sg, &ph));
+        if (!keep(finish_apply(m, nullptr))) return MPS_ECUDA;
+        TRY(run_measure(m, h, 0, m->h_out.data(), false));
+        e2[sgn] = m->h_out[0];
       }
-      g += R[k].scale * (e2[0] - e2[1]) / 2.0;
+      grad[t.sel_i] += t.scale * (e2[0] - e2[1]) / 2.0;
     }
-    grad[i] = g;
+    return rc_all;
   }
-  return MPS_OK;
+  // slot 0 carries the unshifted prefix; each wave forks two slots per target
+  const int wave = (m->n_slots - 1) / 2;
+  std::vector<double> th((size_t)m->n_slots * std::max(1, np));
+  for (int s = 0; s < m->n_slots; ++s)
+    if (np > 0) std::memcpy(&th[(size_t)s * np], theta, (size_t)np * 8);
+  TRY(upload_reset(m, 0, 1, ref.data()));
+  int64_t trunk = 0;
+  for (size_t w0 = 0; w0 < tg.size(); w0 += wave) {
+    const int nw = (int)std::min<size_t>(wave, tg.size() - w0);
+    std::vector<int64_t> start(2 * nw), sgate(2 * nw);
+    std::vector<double> sphi(2 * nw);
+    for (int i = 0; i < nw; ++i) {
+      const Target& t = tg[w0 + i];
+      if (t.gate > trunk) {
+        const int64_t st0 = trunk;
+        TRY(run_circuit(m, c, 0, 1, th.data(), &st0, nullptr, nullptr, t.gate));
+        if (!keep(finish_apply(m, nullptr))) return MPS_ECUDA;
+        trunk = t.gate;
+      }
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        TRY(copy_slot(m, 0, 1 + 2 * i + sgn));
+        start[2 * i + sgn] = t.gate;
+        sgate[2 * i + sgn] = t.gate;
+        sphi[2 * i + sgn] = sgn == 0 ? kHalfPi : -kHalfPi;
+      }
+    }
+    TRY(run_circuit(m, c, 1, 2 * nw, th.data() + np, start.data(), sgate.data(), sphi.data(), G));
+    for (int s = 1; s <= 2 * nw; ++s) {
+      double dw;
+      int st4[4];
+      TRY(read_slot_stats(m, s, &dw, st4));
+      if (st4[1] > 0) rc_all = MPS_ENOCONV;
+    }
+    for (int i = 0; i < nw; ++i) {
+      double e2[2];
+      for (int sgn = 0; sgn < 2; ++sgn) {
+        TRY(run_measure(m, h, 1 + 2 * i + sgn, m->h_out.data(), false));
+        e2[sgn] = m->h_out[0];
+      }
+      const Target& t = tg[w0 + i];
+      grad[t.sel_i] += t.scale * (e2[0] - e2[1]) / 2.0;
+    }
+  }
+  return rc_all;
 }
 
 int mps_get_stats(mps_t m, mps_stats_t* s) {

@@ -248,7 +248,10 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   double dw_acc = 0.0;
   (void)max_sweeps;
 
-  for (int64_t g = g0; g < g1; ++g) {
+  const int64_t g_first = c.start_gate ? max(g0, c.start_gate[blockIdx.x]) : g0;
+  const int64_t g_shift = c.shift_gate ? c.shift_gate[blockIdx.x] : -1;
+  const double phi_shift = c.shift_phi ? c.shift_phi[blockIdx.x] : 0.0;
+  for (int64_t g = g_first; g < g1; ++g) {
     GateRec gr;
     if constexpr (RAW) {
       gr.bond = c.raw_bond[g];
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
         u = A[threadIdx.x];
       } else {
         const Cx<double>* P = (const Cx<double>*)c.mats + 16 * (size_t)gr.m1;
-        const double half = 0.5 * gr.scale * th[gr.param];
+        const double half = 0.5 * (gr.scale * th[gr.param] + (g == g_shift ? phi_shift : 0.0));
         double sn, cs;
         sincos(half, &sn, &cs);
         u = cx(0.0, 0.0);

@@ -33,6 +33,12 @@ struct CircDev {
   const double* mats;  // 32 doubles per matrix (16 complex)
   int n_params;
   const int32_t* raw_bond = nullptr;  // raw-gate launches only: bond of gate g, matrix g of mats
+  // Optional per-block arrays (index blockIdx.x, i.e. slot - slot0): the first gate the
+  // block applies, and a shift added to the rotation angle phi of one parametric gate
+  // (parameter-shift evaluations forked from a shared prefix).
+  const int64_t* start_gate = nullptr;
+  const int64_t* shift_gate = nullptr;
+  const double* shift_phi = nullptr;
 };
 
 // Reset slots [slot0, slot0+count) to product states; occ: [count][n] bytes (0/1).

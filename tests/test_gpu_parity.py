@@ -296,9 +296,26 @@ def test_gradient_parity():
     ref = grad.parameter_shift(e_of_angles, rp, rs, theta, sel)
     H = G.ham_jw_from_integrals(h, g)
     C = G.circ_uccsd(n, ne)
-    M = G.mps_create(n, chi, G.MPS_FP64, n_slots=2)
-    gg = G.vqe_gradient(M, C, H, theta, sel)
-    assert np.abs(gg - ref).max() <= 1e-9
+    one = G.vqe_gradient(G.mps_create(n, chi, G.MPS_FP64, n_slots=1), C, H, theta, sel)
+    assert np.abs(one - ref).max() <= 1e-9
+    # shared-prefix forks: 4 slots (one rotation per wave) and 9 slots (four per wave)
+    for slots in (4, 9):
+        gg = G.vqe_gradient(G.mps_create(n, chi, G.MPS_FP64, n_slots=slots), C, H, theta, sel)
+        assert np.abs(gg - one).max() <= 1e-13
+
+
+def test_gradient_forks_match_restarts_under_truncation():
+    # chi = 4 truncates: the forked route must still reproduce the from-scratch route
+    n, ne, chi = 10, 4, 4
+    h, g = syn.random_integrals(5, 6)
+    H = G.ham_jw_from_integrals(h, g)
+    C = G.circ_uccsd(n, ne)
+    theta = syn.random_amplitudes(C.n_params, 7) * 6
+    sel = [0, C.n_params // 2, C.n_params - 1]
+    for prec, tol in ((G.MPS_FP64, 1e-13), (G.MPS_MIXED, 1e-6)):
+        one = G.vqe_gradient(G.mps_create(n, chi, prec, n_slots=1), C, H, theta, sel)
+        forked = G.vqe_gradient(G.mps_create(n, chi, prec, n_slots=7), C, H, theta, sel)
+        assert np.abs(forked - one).max() <= tol * max(1.0, np.abs(one).max())
 
 
 def test_state_roundtrip():
@@ -311,3 +328,23 @@ def test_state_roundtrip():
         assert np.array_equal(a, b)
     for a, b in zip(lams, st.lam):
         assert np.array_equal(a, b)
+
+
+def test_vqe_loop_reaches_sector_ground_state():
+    # 4 spin orbitals, 2 electrons: UCCSD spans the N = 2, Sz = 0 ground state, and
+    # chi = 4 holds every state exactly, so the loop must reach the sector minimum
+    from paper_2207_03711_gb300 import vqe
+    n, ne, chi = 4, 2, 4
+    h, g = syn.random_integrals(2, 1)
+    Hf = fock.fock_hamiltonian(h, g)
+    Hd = Hf.toarray() if hasattr(Hf, "toarray") else np.asarray(Hf)
+    idx = fock.sector_indices(n, ne)
+    e0 = np.linalg.eigvalsh(Hd[np.ix_(idx, idx)])[0]
+    H = G.ham_jw_from_integrals(h, g)
+    C = G.circ_uccsd(n, ne)
+    M = G.mps_create(n, chi, G.MPS_FP64, n_slots=9)
+    theta0 = syn.random_amplitudes(C.n_params, 2)
+    theta, e, hist = vqe.minimize(M, C, H, theta0, iters=200, gtol=1e-9)
+    assert e >= e0 - 1e-9                      # variational bound
+    assert e - e0 <= 1e-8
+    assert hist[-1][1] <= hist[0][1]
