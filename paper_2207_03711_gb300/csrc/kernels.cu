@@ -156,7 +156,7 @@ __device__ __forceinline__ double flops_per_gate(int rl, int rm, int rr, int k) 
 
 template <class R>
 struct EngineLayout {
-  size_t head, svd, w_off, w_bytes, t_off, t_bytes, total;
+  size_t head, svd, ldw, w_off, w_bytes, t_off, t_bytes, g_bytes, total;
   bool w_smem, t_smem;
   __host__ __device__ EngineLayout(int chi, int nt) {
     const size_t mmax = 2 * (size_t)chi;
@@ -165,15 +165,23 @@ struct EngineLayout {
     svd = sizeof(R) * (2 * mmax + 4 * mmax + 5 * mmax) + sizeof(Cx<R>) * 2 * mmax + (sizeof(R) + 4) * nt +
           (8 + 4) * mmax + 16 + sizeof(R) * nt + 4 * (size_t)chi + 16;
     svd = (svd + 255) & ~(size_t)255;
-    w_bytes = sizeof(R) * ((size_t)chi * (mmax + 1) + (size_t)chi * chi);   // W rows + Gram
+    // singular-vector rows: stride = 8 (mod 32) entries, so that the 8-lane dot products
+    // of four rows in one warp start in four different bank groups
+    ldw = mmax + 1;
+    ldw += (8 + 32 - (ldw & 31)) & 31;
+    w_bytes = sizeof(R) * ((size_t)chi * ldw + (size_t)chi * chi);   // W rows + Gram
+    w_bytes = (w_bytes + 255) & ~(size_t)255;
     t_bytes = sizeof(Cx<R>) * (mmax + 16) * mmax;
-    // the static site-update GEMM tiles (64x17 + 16x65 complex) share the 227 KB
-    const size_t cap = 226 * 1024 - sizeof(Cx<R>) * (64 * 17 + 16 * 65) - 512;
+    // the site-update GEMM tiles (64x17 + 16x65 complex) reuse the T area (T is dead by
+    // then) or take their own area when T lives in global memory
+    g_bytes = sizeof(Cx<R>) * (64 * 17 + 16 * 65);
+    const size_t cap = 227 * 1024 - 1024;
     w_off = head + svd;
     w_smem = w_off + w_bytes <= cap;
     t_off = w_off + (w_smem ? w_bytes : 0);
-    t_smem = t_off + t_bytes <= cap;
-    total = t_off + (t_smem ? t_bytes : 0);
+    const size_t t_area = t_bytes > g_bytes ? t_bytes : g_bytes;
+    t_smem = t_off + t_area <= cap;
+    total = t_off + (t_smem ? t_area : g_bytes);
   }
 };
 
@@ -213,8 +221,9 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   int* order = (int*)(sig2d + mmax);
   R* grid = (R*)(order + mmax);              // NT log-spaced bisection shifts / smax
   int* iters_of = (int*)(grid + NT);         // bisection passes for kk = 1..chi
-  __shared__ Cx<R> gA[64][17];
-  __shared__ Cx<R> gB[16][65];
+  Cx<R>(*gA)[17] = reinterpret_cast<Cx<R>(*)[17]>(smem + L.t_off);
+  Cx<R>(*gB)[65] = reinterpret_cast<Cx<R>(*)[65]>(smem + L.t_off + sizeof(Cx<R>) * 64 * 17);
+  const int ldw = (int)L.ldw;
   R* Wv = TS ? (R*)(smem + L.w_off) : (R*)((double*)m.work_S + (size_t)s * 16 * chi * chi + 8 * chi * chi);
   Cx<R>* T = TS ? (Cx<R>*)(smem + L.t_off) : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 16);
   const double* th = theta + (size_t)blockIdx.x * c.n_params;
@@ -400,18 +409,35 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
       const R delta = R(8) * (hi[t] - lo[t]) + R(4) * Eps<R>::v * smax;
       owning_block<R>(b2, 2 * tp, sig, t, delta, tiny, &s0, &e0);
       twisted_vector<R>(bb, tp, s0, e0, sig[t], tiny, dp, dp + (size_t)2 * tp * k, k, tall ? 0 : 1,
-                        Wv + (size_t)t * (mmax + 1));
+                        Wv + (size_t)t * ldw);
     }
     if (threadIdx.x == 0) misc[1] = 0;
     __syncthreads();
     PHASE(3);
-    orthonormalize_rows_block<R, NT>(Wv, mmax + 1, k, tp, Wv + (size_t)chi * (mmax + 1), xs, &misc[1]);
+    orthonormalize_rows_block<R, NT>(Wv, ldw, k, tp, Wv + (size_t)chi * ldw, xs, &misc[1]);
     PHASE(4);
     Cx<R>* xout = (Cx<R>*)scratch;               // k x ncol right singular vectors v_t
     int kf = k;                                  // kept count of the path taken
     if (misc[1] == 0) {
       // (5) back-transformation: x_t = P w_t (tall) or Q [w_t; 0] (wide) is the right
-      //     singular vector v_t of M' (length ncol); 16 entries per thread.
+      //     singular vector v_t of M' (length ncol); 16 entries per thread. First the
+      //     stored reflectors are turned into their vectors in place (tail times scale,
+      //     conjugated for the right reflectors; 1 at the start), which the unused
+      //     factor array of the other side holds meanwhile.
+      const int nref = tall ? tp - 1 : tp;
+      Cx<R>* scl = tall ? tauL : tauR;
+      for (int jr = threadIdx.x; jr < nref; jr += NT)
+        scl[jr] = tall ? T[(size_t)(jr + 1) * ld + jr] : T[(size_t)jr * ld + jr];
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nref * ncol; idx += NT) {
+        // consecutive threads walk consecutive shared-memory entries
+        const int jr = tall ? idx % nref : idx / ncol, q = tall ? idx / nref : idx % ncol;
+        const int start = tall ? jr + 1 : jr;
+        if (q < start) continue;
+        Cx<R>& e = tall ? T[(size_t)q * ld + jr] : T[(size_t)jr * ld + q];
+        e = q == start ? cx<R>(1, 0) : (tall ? conj(e) * scl[jr] : e * scl[jr]);
+      }
+      __syncthreads();
       int LV = 8;
       while (LV < 32 && LV * 16 < ncol) LV <<= 1;
       const int vpp = NT / LV;
@@ -424,14 +450,12 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
         for (int e = 0; e < 16; ++e) {
           const int q = l + e * LV;
           R val = R(0);
-          if (act && q < tp) val = Wv[(size_t)t * (mmax + 1) + q];
+          if (act && q < tp) val = Wv[(size_t)t * ldw + q];
           x[e] = cx<R>(val, R(0));
         }
-        const int nref = tall ? tp - 1 : tp;
         for (int jr = nref - 1; jr >= 0; --jr) {
           const int start = tall ? jr + 1 : jr;
           const Cx<R> tau = tall ? tauR[jr] : tauL[jr];
-          const Cx<R> scj = tall ? T[(size_t)(jr + 1) * ld + jr] : T[(size_t)jr * ld + jr];
           // entry e covers q in [e LV, e LV + LV); entries wholly above the reflector's
           // start are zero and skipped (the test is uniform over the block)
           Cx<R> hv[16];
@@ -441,9 +465,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
             hv[e] = cx<R>(0, 0);
             if ((e + 1) * LV > start) {
               const int q = l + e * LV;
-              if (q > start && q < ncol)
-                hv[e] = tall ? conj(T[(size_t)q * ld + jr]) * scj : T[(size_t)jr * ld + q] * scj;
-              if (q == start) hv[e] = cx<R>(1, 0);
+              if (q >= start && q < ncol) hv[e] = tall ? T[(size_t)q * ld + jr] : T[(size_t)jr * ld + q];
               cmac_conj(sdot, hv[e], x[e]);
             }
           }

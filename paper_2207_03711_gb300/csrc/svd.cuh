@@ -415,34 +415,54 @@ __device__ void orthonormalize_rows_block(R* W, int ldw, int k, int p, R* coef, 
         if (act && l == 0) small[i * 8 + j] = acc;
       }
       __syncthreads();
-      // Cholesky factor L (in place) and its inverse X = L^{-1} at small + 64; one thread
+      // Cholesky factor L and its inverse X = L^{-1} (written to small + 64); one thread,
+      // the 8 x 8 factor kept in registers (all indices compile-time)
       if (tid == 0) {
-        R* G = small;
-        R* X = small + 64;
-        for (int j = 0; j < nb; ++j) {
-          const R gjj = G[j * 8 + j];
-          R d = gjj;
-          for (int u = 0; u < j; ++u) d -= G[j * 8 + u] * G[j * 8 + u];
-          if (!(d > R(1e-6) * gjj)) {
-            ++*collapsed;
-            d = gjj > R(0) ? gjj * R(1e-30) : R(1e-30);
+        R Lm[8][8], Xm[8][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            Lm[i][j] = (j <= i && i < nb) ? small[i * 8 + j] : R(0);
+            Xm[i][j] = R(0);
           }
-          const R ljj = sqrt(d);
-          G[j * 8 + j] = ljj;
-          for (int i = j + 1; i < nb; ++i) {
-            R v = G[i * 8 + j];
-            for (int u = 0; u < j; ++u) v -= G[i * 8 + u] * G[j * 8 + u];
-            G[i * 8 + j] = v / ljj;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (j < nb) {
+            const R gjj = Lm[j][j];
+            R d = gjj;
+#pragma unroll
+            for (int u = 0; u < j; ++u) d -= Lm[j][u] * Lm[j][u];
+            if (!(d > R(1e-6) * gjj)) {
+              ++*collapsed;
+              d = gjj > R(0) ? gjj * R(1e-30) : R(1e-30);
+            }
+            const R ljj = sqrt(d), inv = R(1) / ljj;
+            Lm[j][j] = ljj;
+#pragma unroll
+            for (int i = j + 1; i < 8; ++i) {
+              R v = Lm[i][j];
+#pragma unroll
+              for (int u = 0; u < j; ++u) v -= Lm[i][u] * Lm[j][u];
+              Lm[i][j] = v * inv;
+            }
           }
         }
-        for (int j = 0; j < nb; ++j) {
-          X[j * 8 + j] = R(1) / G[j * 8 + j];
-          for (int i = j + 1; i < nb; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          Xm[j][j] = R(1) / Lm[j][j];
+#pragma unroll
+          for (int i = j + 1; i < 8; ++i) {
             R v = 0;
-            for (int u = j; u < i; ++u) v += G[i * 8 + u] * X[u * 8 + j];
-            X[i * 8 + j] = -v / G[i * 8 + i];
+#pragma unroll
+            for (int u = j; u < i; ++u) v += Lm[i][u] * Xm[u][j];
+            Xm[i][j] = -v / Lm[i][i];
           }
         }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) small[64 + i * 8 + j] = Xm[i][j];
       }
       __syncthreads();
       // W_b <- X W_b, one thread per column
