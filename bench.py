@@ -35,6 +35,11 @@ WORKLOAD = {"workload": "uccsd_24q_12e_chi64_single_eval", "qubits": N_QUBITS, "
             "theta_seed": SEED, "evals_per_call": 1}
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of k_circuit in the 256-gate profile case
+# (ncu capture of the current kernel; None until one exists)
+TRAFFIC_PROFILE_CASE = None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,8 +308,10 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      # DRAM bytes per launch: the ncu capture of the 256-gate profile case
-                     # (1.221 MB read + 0.073 MB written) scaled by the gates per launch
-                     "traffic": (1.221e6 + 0.073e6) / 256 * (442272 / n_launch),
+                     # (TRAFFIC_PROFILE_CASE bytes) scaled by the gates per launch; None
+                     # while no capture of the current kernel exists
+                     "traffic": (TRAFFIC_PROFILE_CASE / 256 * (442272 / n_launch)
+                                 if TRAFFIC_PROFILE_CASE is not None else None),
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 256-gate "
                                        "profile case, scaled to the mean gates per launch",
                      "kernel": "k_circuit<float,512>", "launches_per_step": n_launch,

@@ -307,21 +307,19 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
 
     // (2) Eq. (7): M[(a,i),(j,c)] = sum_{i'j'} U[ij,i'j'] sum_b B_n[a,i',b] B_{n+1}[b,j',c];
     //     W <- M; Eq. (8): M' = lambda_{n-1}[a] M, stored tall in T (M' or M'^H).
+    //     Theta = B_n (2 r_l x r_m) . B_{n+1} (r_m x 2 r_r) by the tiled GEMM into W, then
+    //     the gate on each (i, j) quad in place
+    {
+      GemmTerm<R> gt{Bn, rm, false, Bn1, 2 * rr, cx<R>(1, 0), false};
+      block_gemm<R, NT>(mrows, ncol, rm, &gt, 1, W, ncol, gA, gB);
+    }
+    __syncthreads();
     double fro = 0.0;
     for (int it = threadIdx.x; it < rl * rr; it += NT) {
       const int a = it / rr, cc = it - a * rr;
-      Cx<R> t00 = cx<R>(0, 0), t01 = t00, t10 = t00, t11 = t00;
-      const Cx<R>* x0p = Bn + (size_t)(2 * a) * rm;
-      const Cx<R>* x1p = x0p + rm;
-      for (int b = 0; b < rm; ++b) {
-        const Cx<R> x0 = x0p[b], x1 = x1p[b];
-        const Cx<R> y0 = Bn1[(size_t)(2 * b) * rr + cc], y1 = Bn1[(size_t)(2 * b + 1) * rr + cc];
-        cmac(t00, x0, y0);
-        cmac(t01, x0, y1);
-        cmac(t10, x1, y0);
-        cmac(t11, x1, y1);
-      }
-      const Cx<R> th4[4] = {t00, t01, t10, t11};
+      Cx<R>* w0 = W + (size_t)(2 * a) * ncol + cc;
+      Cx<R>* w1 = w0 + ncol;
+      const Cx<R> th4[4] = {w0[0], w0[rr], w1[0], w1[rr]};
       const R la = laml ? (R)laml[a] : R(1);
 #pragma unroll
       for (int ij = 0; ij < 4; ++ij) {

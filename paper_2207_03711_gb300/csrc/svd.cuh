@@ -299,38 +299,67 @@ __device__ void twisted_vector(const R* b, int p, int s0, int e0, R lam, R tiny,
     prev = -lam - qdiv(b[i - 1] * b[i - 1], prev);
     dp[(size_t)i * stride] = prev;
   }
-  // backward pass fused with the twist search: gamma_i = dp_i + dm_i + lam
+  // backward pass fused with the twist search: gamma_i = dp_i + dm_i + lam. The scratch
+  // lives in global memory, so its reads are issued 8 at a time ahead of their use.
+  constexpr int PF = 8;
   int rr = e0 - 1;
   R nxt = -lam;
   dm[(size_t)(e0 - 1) * stride] = nxt;
   R best = rabs(dp[(size_t)(e0 - 1) * stride] + nxt + lam);
-  for (int i = e0 - 2; i >= s0; --i) {
-    R q = nxt;
-    if (rabs(q) < tiny) q = -tiny;
-    nxt = -lam - qdiv(b[i] * b[i], q);
-    dm[(size_t)i * stride] = nxt;
-    const R g = rabs(dp[(size_t)i * stride] + nxt + lam);
-    if (g < best) {
-      best = g;
-      rr = i;
+  for (int i0 = e0 - 2; i0 >= s0; i0 -= PF) {
+    R dpv[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) dpv[u] = i0 - u >= s0 ? dp[(size_t)(i0 - u) * stride] : R(0);
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int i = i0 - u;
+      if (i >= s0) {
+        R q = nxt;
+        if (rabs(q) < tiny) q = -tiny;
+        nxt = -lam - qdiv(b[i] * b[i], q);
+        dm[(size_t)i * stride] = nxt;
+        const R g = rabs(dpv[u] + nxt + lam);
+        if (g < best) {
+          best = g;
+          rr = i;
+        }
+      }
     }
   }
   // z_rr = 1; z_i = -(b_i / dp_i) z_{i+1} below, z_i = -(b_{i-1} / dm_i) z_{i-1} above
   for (int q = 0; q < p; ++q) w[q] = R(0);
   R z = 1;
   if ((rr & 1) == odd) w[rr >> 1] = z;
-  for (int i = rr - 1; i >= s0; --i) {
-    R d = dp[(size_t)i * stride];
-    if (rabs(d) < tiny) d = -tiny;
-    z = -qdiv(b[i], d) * z;
-    if ((i & 1) == odd) w[i >> 1] = z;
+  for (int i0 = rr - 1; i0 >= s0; i0 -= PF) {
+    R dv[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) dv[u] = i0 - u >= s0 ? dp[(size_t)(i0 - u) * stride] : R(1);
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int i = i0 - u;
+      if (i >= s0) {
+        R d = dv[u];
+        if (rabs(d) < tiny) d = -tiny;
+        z = -qdiv(b[i], d) * z;
+        if ((i & 1) == odd) w[i >> 1] = z;
+      }
+    }
   }
   z = 1;
-  for (int i = rr + 1; i < e0; ++i) {
-    R d = dm[(size_t)i * stride];
-    if (rabs(d) < tiny) d = -tiny;
-    z = -qdiv(b[i - 1], d) * z;
-    if ((i & 1) == odd) w[i >> 1] = z;
+  for (int i0 = rr + 1; i0 < e0; i0 += PF) {
+    R dv[PF];
+#pragma unroll
+    for (int u = 0; u < PF; ++u) dv[u] = i0 + u < e0 ? dm[(size_t)(i0 + u) * stride] : R(1);
+#pragma unroll
+    for (int u = 0; u < PF; ++u) {
+      const int i = i0 + u;
+      if (i < e0) {
+        R d = dv[u];
+        if (rabs(d) < tiny) d = -tiny;
+        z = -qdiv(b[i - 1], d) * z;
+        if ((i & 1) == odd) w[i >> 1] = z;
+      }
+    }
   }
   R nrm = 0;
   for (int q = 0; q < p; ++q) nrm += w[q] * w[q];

@@ -161,6 +161,34 @@ def test_truncated_step_parity_24q(prec):
         assert np.abs(ev_g - ev_o).max() <= ev_tol
 
 
+@pytest.mark.parametrize("prec", [G.MPS_FP64, G.MPS_MIXED])
+def test_truncated_step_parity_chi128(prec):
+    """chi = 128: the 256 x 256 M' of the middle bonds lives in global memory (the
+    engine's second layout); single steps from an oracle-made canonical state."""
+    n, chi = 16, 128
+    st0 = _canon_state(n, chi, 4)
+    rng = np.random.default_rng(5)
+    M = G.mps_create(n, chi, prec)
+    lam_tol, blk_tol = (1e-12, 1e-10) if prec == G.MPS_FP64 else (2e-5, 2e-4)
+    for bond in (7, 6, 8):
+        U, _ = np.linalg.qr(rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4)))
+        st = st0.copy()
+        G.mps_set_state(M, st.B, st.lam)
+        dw_gpu = G.mps_apply_gates(M, [bond], U[None])
+        dw_or = mps.apply_two_site(st, bond, U, chi)
+        r, sites, lams = G.mps_get_state(M)
+        assert r[bond] == len(st.lam[bond])
+        assert np.abs(lams[bond] - st.lam[bond]).max() <= lam_tol
+        assert abs(dw_gpu - dw_or) <= max(lam_tol, 1e-12)
+        ll = st.lam[bond - 1]
+        blk_g = ll[:, None, None, None] * np.einsum("aib,bjc->aijc", sites[bond], sites[bond + 1])
+        blk_o = ll[:, None, None, None] * np.einsum("aib,bjc->aijc", st.B[bond], st.B[bond + 1])
+        assert np.linalg.norm(blk_g - blk_o) / np.linalg.norm(blk_o) <= blk_tol
+        # the new right site is right-canonical: rows of V orthonormal
+        V = sites[bond + 1].reshape(r[bond], -1)
+        assert np.abs(V @ V.conj().T - np.eye(r[bond])).max() <= (1e-12 if prec == G.MPS_FP64 else 2e-6)
+
+
 def test_measurement_parity_full_size():
     """All 29 737 strings of the 24-qubit Hamiltonian on a fixed chi = 64 MPS; a seeded
     sample of 400 terms is checked one by one against the oracle."""
