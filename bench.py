@@ -16,6 +16,7 @@ vqe_energy call in the mixed-precision mode.
 bounded, stratified sample of the same workload instead.
 """
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -37,7 +38,7 @@ WORKLOAD = {"workload": "uccsd_24q_12e_chi64_single_eval", "qubits": N_QUBITS, "
 
 # dram__bytes_read.sum + dram__bytes_write.sum of k_circuit in the 256-gate profile case
 # (ncu capture of the current kernel; None until one exists)
-TRAFFIC_PROFILE_CASE = None
+TRAFFIC_PROFILE_CASE = 1.175808e6 + 0.070656e6
 
 
 def parse():
@@ -46,6 +47,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--serve", action="store_true",
+                    help="serving stream: Poisson arrivals of mixed energy/gradient requests")
+    ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--profile-case", action="store_true",
                     help="small profiling case: 256 gates on a saturated chi=64 state + one measurement")
     return ap.parse_args()
@@ -358,8 +362,66 @@ def run_profile_case():
                       "kernel_launches": s["kernel_launches"]}))
 
 
+def run_serve(args):
+    """Serving stream (scaled-down form of the mixed-size request workload): energy and
+    gradient requests with qubits uniform in {12, 14, ..., 24}, chi in {16, 32, 64},
+    circuit = singles + the first 32 doubles, random integrals per request. A closed-loop
+    burst of 24 requests measures the saturation rate; the rest arrive as a Poisson
+    stream at 0.7 of it. Prints one JSON line with throughput and p50/p99 latency."""
+    import paper_2207_03711_gb300 as G
+    from paper_2207_03711_gb300 import synthetic as syn
+    from paper_2207_03711_gb300.serve import Request, Server
+    G.build()
+    G.load_library()
+    rng = np.random.default_rng(SEED)
+    n_doubles = 32
+
+    def make(i):
+        n = int(rng.choice(np.arange(12, 26, 2)))
+        ne = n // 2
+        chi = int(rng.choice([16, 32, 64]))
+        h, g = syn.random_integrals(n // 2, 1000 + i)
+        n_singles = 2 * (ne // 2) * ((n - ne) // 2)
+        theta = syn.random_amplitudes(n_singles + n_doubles, 2000 + i)
+        if rng.random() < 0.2:
+            sel = n_singles + rng.choice(n_doubles, 4, replace=False)
+            return Request("gradient", h, g, ne, chi, theta, sel=sel, n_slots=9, n_doubles=n_doubles, tag=i)
+        return Request("energy", h, g, ne, chi, theta, n_doubles=n_doubles, tag=i)
+
+    reqs = [make(i) for i in range(max(args.serve_requests, 30))]
+    kinds = collections.Counter(r.kind for r in reqs)
+    burst = reqs[:24]
+    with Server(max_inflight=32) as srv:
+        t0 = time.perf_counter()
+        for f in [srv.submit(r) for r in burst]:
+            f.result()
+        sat = len(burst) / (time.perf_counter() - t0)
+    rate = 0.7 * sat
+    arr = np.random.default_rng(SEED + 1).exponential(1.0 / rate, size=len(reqs) - len(burst))
+    with Server(max_inflight=32) as srv:
+        t_next = time.perf_counter()
+        futs = []
+        for r, dt in zip(reqs[len(burst):], arr):
+            t_next += dt
+            pause = t_next - time.perf_counter()
+            if pause > 0:
+                time.sleep(pause)
+            futs.append(srv.submit(r))
+        for f in futs:
+            f.result()
+        st = srv.stats()
+    print(json.dumps({"metric": "serving stream", "requests": len(reqs) - len(burst),
+                      "kinds": dict(kinds), "saturation_req_per_s": sat, "arrival_rate_req_per_s": rate,
+                      **st, "config": {"qubits": "uniform {12,...,24}", "chi": "{16, 32, 64}",
+                                       "circuit": "singles + first 32 doubles", "precision": "mixed",
+                                       "gradient": "4 doubles, 9 slots"}}))
+
+
 def main():
     args = parse()
+    if args.serve:
+        run_serve(args)
+        return
     if args.profile_case:
         run_profile_case()
     elif args.impl == "reference":

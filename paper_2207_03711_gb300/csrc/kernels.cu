@@ -177,10 +177,11 @@ struct EngineLayout {
     g_bytes = sizeof(Cx<R>) * (64 * 17 + 16 * 65);
     const size_t cap = 227 * 1024 - 1024;
     w_off = head + svd;
-    w_smem = w_off + w_bytes <= cap;
+    // W goes to shared memory only if the GEMM tiles still fit behind it
+    w_smem = w_off + w_bytes + g_bytes <= cap;
     t_off = w_off + (w_smem ? w_bytes : 0);
     const size_t t_area = t_bytes > g_bytes ? t_bytes : g_bytes;
-    t_smem = t_off + t_area <= cap;
+    t_smem = w_smem && t_off + t_area <= cap;
     total = t_off + (t_smem ? t_area : g_bytes);
   }
 };

@@ -4,9 +4,9 @@
 // own SVD also starts from a bidiagonal reduction), then the singular values of the
 // real bidiagonal B from Sturm counts of its Golub-Kahan tridiagonal
 // TGK = [[0, B], [B^T, 0]] (multisection bisection), singular vectors of B from a
-// twisted factorisation of TGK - sigma I, re-orthonormalisation (classical
-// Gram-Schmidt twice, in descending sigma order), and back-transformation by the
-// stored Householder reflectors.
+// twisted factorisation of TGK - sigma I, re-orthonormalisation (block classical
+// Gram-Schmidt twice with Cholesky QR inside each block of 8, in descending sigma
+// order), and back-transformation by the stored Householder reflectors.
 //
 // Conventions: the reflector H = I - tau v v^H (v_0 = 1) satisfies H^H x = beta e_1
 // with beta real. T (r x p, r >= p, column-major, leading dimension ld) is reduced

@@ -18,18 +18,32 @@ import time
 
 import numpy as np
 
-from . import (MPS_MIXED, circ_uccsd, ham_jw_from_integrals, mps_create, mps_estimate_bytes,
-               vqe_energy, vqe_gradient)
+from . import (MPS_MIXED, circ_create, circ_get_rotations, circ_set_reference, circ_uccsd,
+               ham_jw_from_integrals, mps_create, mps_estimate_bytes, vqe_energy, vqe_gradient)
+
+
+def uccsd_circuit(n_qubits, n_electrons, n_doubles=None):
+    """The UCCSD circuit, or (n_doubles given) its singles plus the first n_doubles
+    doubles in canonical order, on the Hartree-Fock reference."""
+    full = circ_uccsd(n_qubits, n_electrons)
+    if n_doubles is None:
+        return full
+    n_singles = 2 * (n_electrons // 2) * ((n_qubits - n_electrons) // 2)
+    paulis, pidx, scale = circ_get_rotations(full)
+    keep = pidx < n_singles + n_doubles
+    c = circ_create(paulis[keep], pidx[keep], scale[keep])
+    circ_set_reference(c, np.array([1] * n_electrons + [0] * (n_qubits - n_electrons), dtype=np.uint8))
+    return c
 
 
 class Request:
     """kind: "energy" or "gradient"; h, eri: spatial-orbital integrals (chemist order);
     theta: UCCSD amplitudes; sel: parameter indices of a gradient request; n_slots:
     slots of the gradient's handle (shared-prefix forks run (n_slots - 1) / 2 rotations
-    per pass)."""
+    per pass); n_doubles: keep the singles and the first n_doubles doubles only."""
 
     def __init__(self, kind, h, eri, n_electrons, chi, theta, precision=MPS_MIXED, sel=None, n_slots=None,
-                 tag=None):
+                 tag=None, n_doubles=None):
         if kind not in ("energy", "gradient"):
             raise ValueError(f"unknown request kind {kind!r}")
         self.kind, self.h, self.eri = kind, np.asarray(h), np.asarray(eri)
@@ -38,6 +52,7 @@ class Request:
         self.sel = None if sel is None else np.asarray(sel, dtype=np.int32)
         self.n_slots = n_slots if n_slots is not None else (1 if kind == "energy" else 9)
         self.tag = tag
+        self.n_doubles = n_doubles
         self.n_qubits = 2 * self.h.shape[0]
 
 
@@ -81,7 +96,7 @@ class Server:
         it.ham = it.circ = None
         if need_bytes is None:
             it.ham = ham_jw_from_integrals(req.h, req.eri)
-            it.circ = circ_uccsd(req.n_qubits, req.n_electrons)
+            it.circ = uccsd_circuit(req.n_qubits, req.n_electrons, req.n_doubles)
             need_bytes = mps_estimate_bytes(req.n_qubits, req.chi, req.precision, req.n_slots, it.circ, it.ham)
         it.need = int(need_bytes)
         if it.need > self.budget:
