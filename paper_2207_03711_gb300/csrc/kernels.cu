@@ -10,6 +10,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "cx.cuh"
 #include "kernels.cuh"
@@ -455,18 +456,16 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
         for (int jr = nref - 1; jr >= 0; --jr) {
           const int start = tall ? jr + 1 : jr;
           const Cx<R> tau = tall ? tauR[jr] : tauL[jr];
-          // entry e covers q in [e LV, e LV + LV); entries wholly above the reflector's
-          // start are zero and skipped (the test is uniform over the block)
+          // every entry is processed (zeros above the start): skipping the leading
+          // entries with a block-uniform test was measured slower than the work saved
           Cx<R> hv[16];
           Cx<R> sdot = cx<R>(0, 0);
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            hv[e] = cx<R>(0, 0);
-            if ((e + 1) * LV > start) {
-              const int q = l + e * LV;
-              if (q >= start && q < ncol) hv[e] = tall ? T[(size_t)q * ld + jr] : T[(size_t)jr * ld + q];
-              cmac_conj(sdot, hv[e], x[e]);
-            }
+            const int q = l + e * LV;
+            hv[e] = (q >= start && q < ncol) ? (tall ? T[(size_t)q * ld + jr] : T[(size_t)jr * ld + q])
+                                             : cx<R>(0, 0);
+            cmac_conj(sdot, hv[e], x[e]);
           }
           for (int o = 1; o < LV; o <<= 1) {
             sdot.x += __shfl_xor_sync(0xffffffffu, sdot.x, o, LV);
@@ -474,8 +473,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
           }
           const Cx<R> f = tau * sdot;
 #pragma unroll
-          for (int e = 0; e < 16; ++e)
-            if ((e + 1) * LV > start) x[e] = x[e] - f * hv[e];
+          for (int e = 0; e < 16; ++e) x[e] = x[e] - f * hv[e];
         }
         if (act) {
 #pragma unroll
@@ -573,19 +571,37 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   }
 }
 
+// The dynamic shared-memory limit of a kernel is process-wide state: handles of
+// different chi launch the same instantiation from several threads, so the limit is
+// raised once to the device's opt-in maximum and never lowered.
+template <auto Kernel>
+static cudaError_t raise_smem_limit() {
+  static std::once_flag once[64];
+  static cudaError_t status[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::call_once(once[dev], [dev] {
+    int optin = 0;
+    status[dev] = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (status[dev] == cudaSuccess)
+      status[dev] = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  });
+  return status[dev];
+}
+
 template <class R, int NT>
 static cudaError_t launch_circ_t(const DevMPS& m, const CircDev& c, int64_t g0, int64_t g1,
                                  int slot0, int count, const double* theta, double cutoff,
                                  int max_sweeps, cudaStream_t st) {
   const EngineLayout<R> L(m.chi, NT);
   if (L.w_smem && L.t_smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_circuit<R, NT, false, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    cudaError_t e = raise_smem_limit<k_circuit<R, NT, false, true>>();
     if (e != cudaSuccess) return e;
     k_circuit<R, NT, false, true><<<count, NT, L.total, st>>>(m, c, g0, g1, slot0, theta, cutoff, max_sweeps);
   } else {
-    cudaError_t e = cudaFuncSetAttribute(k_circuit<R, NT, false, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+    cudaError_t e = raise_smem_limit<k_circuit<R, NT, false, false>>();
     if (e != cudaSuccess) return e;
     k_circuit<R, NT, false, false><<<count, NT, L.total, st>>>(m, c, g0, g1, slot0, theta, cutoff, max_sweeps);
   }
@@ -926,9 +942,7 @@ extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors
     set_error_message("mps_apply_gates_noalloc: gate workspace does not fit in shared memory");
     return MPS_EINVAL;
   }
-  if (cudaFuncSetAttribute(k_circuit<float, 512, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)L.total) != cudaSuccess)
-    return MPS_ECUDA;
+  if (raise_smem_limit<k_circuit<float, 512, true, true>>() != cudaSuccess) return MPS_ECUDA;
   const double* theta = (const double*)(base + off_dw + 128);   // never read: every gate is fixed
   for (int64_t g0 = 0; g0 < n_gates; g0 += 16384) {
     const int64_t g1 = g0 + 16384 < n_gates ? g0 + 16384 : n_gates;
