@@ -121,8 +121,10 @@ int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_str
 int mps_reset(mps_t mps, int slot, const uint8_t* occ);
 
 /* Truncation controls (Eq. 9): keep k = min(chi, #{sigma > cutoff * sigma_0}).
- * Defaults: cutoff 1e-13 (FP64) or 2^-20 (mixed). max_sweeps is accepted for
- * interface stability and bounds no loop of the current SVD (which is direct). */
+ * Defaults: cutoff 1e-13 (FP64) or 2^-20 (mixed). max_sweeps (default 60) caps the
+ * sweeps of the one-sided Jacobi SVD that replaces the bidiagonal route for a gate
+ * whose spectrum is numerically degenerate without a split; a gate that reaches the
+ * cap is counted in n_svd_noconv and the call returns MPS_ENOCONV. */
 int mps_set_svd_params(mps_t mps, double cutoff, int max_sweeps);
 
 /* Sec. III-A, Eqs. (7)-(10), for every gate of circ on slot 0 in order: contract
@@ -181,7 +183,7 @@ int vqe_gradient(mps_t mps, circ_t circ, ham_t ham, const double* theta, int n_s
 typedef struct {
   double discarded_weight; /* summed discarded fraction, slot 0                   */
   int32_t max_rank;        /* largest bond rank reached, slot 0                   */
-  int32_t max_sweeps;      /* bisection passes of the last SVD                     */
+  int32_t max_sweeps;      /* most bisection refinement passes of one gate        */
   int64_t n_gates;         /* gates applied per slot                               */
   int64_t n_svd_noconv;    /* Jacobi fallbacks that hit their sweep cap            */
   double ms_circuit;       /* CUDA-event time of the circuit kernels               */

@@ -109,7 +109,7 @@ struct mps_s {
   int64_t* d_shift_gate = nullptr;
   double* d_shift_val = nullptr;
   double cutoff = 1e-13;
-  int max_sweeps = 40;
+  int max_sweeps = 60;
   mps_stats_t stats{};
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<double> h_out;

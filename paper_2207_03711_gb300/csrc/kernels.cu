@@ -257,7 +257,6 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     }                                              \
   } while (0)
   double dw_acc = 0.0;
-  (void)max_sweeps;
 
   const int64_t g_first = c.start_gate ? max(g0, c.start_gate[blockIdx.x]) : g0;
   const int64_t g_shift = c.shift_gate ? c.shift_gate[blockIdx.x] : -1;
@@ -503,7 +502,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
       }
       __syncthreads();
       const double zero2 = (double)Eps<R>::v * Eps<R>::v * 16.0 * red[NT / 32];
-      jacobi_columns<R, NT, 8>(X, ldx, mrows, ncol, zero2, 60, &misc[2]);
+      jacobi_columns<R, NT, 8>(X, ldx, mrows, ncol, zero2, max_sweeps, &misc[2]);
       for (int p = threadIdx.x; p < mrows; p += NT) {
         double acc = 0.0;
         for (int q = 0; q < ncol; ++q) acc += (double)norm2(X[(size_t)p * ldx + q]);
@@ -946,7 +945,7 @@ extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors
   const double* theta = (const double*)(base + off_dw + 128);   // never read: every gate is fixed
   for (int64_t g0 = 0; g0 < n_gates; g0 += 16384) {
     const int64_t g1 = g0 + 16384 < n_gates ? g0 + 16384 : n_gates;
-    k_circuit<float, 512, true, true><<<1, 512, L.total, st>>>(d, c, g0, g1, 0, theta, std::ldexp(1.0, -20), 40);
+    k_circuit<float, 512, true, true><<<1, 512, L.total, st>>>(d, c, g0, g1, 0, theta, std::ldexp(1.0, -20), 60);
     if (cudaGetLastError() != cudaSuccess) return MPS_ECUDA;
   }
   if (discarded_weight) {

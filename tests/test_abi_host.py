@@ -117,3 +117,24 @@ def test_argument_errors_are_status_codes():
     bad = np.array([[1.0, 2.0], [2.0, 1.0]])
     eri = np.zeros((2,) * 4)
     assert G.ham_get_terms(G.ham_jw_from_integrals(bad, eri))[0].shape[0] > 0
+
+
+def test_estimate_bytes_host_only():
+    """mps_estimate_bytes needs no GPU: it grows with slots, chi and precision, adds the
+    circuit and Hamiltonian buffers, and rejects bad sizes."""
+    G.load_library()
+    base = G.mps_estimate_bytes(12, 16, G.MPS_MIXED, 1)
+    assert base > 0
+    assert G.mps_estimate_bytes(12, 16, G.MPS_MIXED, 4) > base
+    assert G.mps_estimate_bytes(12, 32, G.MPS_MIXED, 1) > base
+    assert G.mps_estimate_bytes(12, 16, G.MPS_FP64, 1) > base
+    h, g = syn.random_integrals(6, 0)
+    H = G.ham_jw_from_integrals(h, g)
+    C = G.circ_uccsd(12, 6)
+    full = G.mps_estimate_bytes(12, 16, G.MPS_MIXED, 1, C, H)
+    assert full > G.mps_estimate_bytes(12, 16, G.MPS_MIXED, 1, C) > base
+    # site tensors alone: sum of cap_{k-1} * 2 * cap_k complex64 entries
+    caps = [1] + [min(16, 2 ** min(b + 1, 11 - b)) for b in range(11)] + [1]
+    assert base >= 8 * sum(caps[k] * 2 * caps[k + 1] for k in range(12))
+    with pytest.raises(G.MpsError):
+        G.mps_estimate_bytes(12, 0, G.MPS_MIXED, 1)
