@@ -38,7 +38,7 @@ WORKLOAD = {"workload": "uccsd_24q_12e_chi64_single_eval", "qubits": N_QUBITS, "
 
 # dram__bytes_read.sum + dram__bytes_write.sum of k_circuit in the 256-gate profile case
 # (ncu capture of the current kernel; None until one exists)
-TRAFFIC_PROFILE_CASE = 1.175808e6 + 0.070656e6
+TRAFFIC_PROFILE_CASE = 1.599744e6 + 0.093440e6
 
 
 def parse():
