@@ -272,8 +272,6 @@ static int ensure_meas(mps_s* m, int32_t nodes, int64_t terms) {
   return MPS_OK;
 }
 
-// Apply gates [0, n_gates) of circ to slots [slot0, slot0 + count); thetas: count x n_params
-// (host). shifts: optional per-slot (gate index, extra angle) for parameter shifts.
 // Apply the circuit to slots [slot0, slot0 + count) with per-slot parameters thetas
 // ([count][n_params], host; null keeps the device copy). Optional per-slot host arrays:
 // start (first gate), shift_gate / shift_phi (angle shift of one parametric gate).

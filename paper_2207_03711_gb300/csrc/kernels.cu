@@ -3,7 +3,8 @@
 //  k_reset        product-state reference (Sec. III-D: X gates on the occupied qubits).
 //  k_circuit      persistent per-slot gate engine: for each two-site gate,
 //                 Eq. (7) contraction, Eq. (8) row scaling by lambda_{n-1}, Eq. (9)
-//                 truncated SVD by one-sided (Hestenes) Jacobi, Eq. (10) updates.
+//                 truncated SVD (bidiagonal route of svd.cuh, one-sided Jacobi for
+//                 spectra that stay degenerate), Eq. (10) updates.
 //  k_right_envs   right identity environments R_k and B^_k = B_k R_{k+1}.
 //  k_level_T/child/close   one level of the Pauli-string prefix trie (Eq. 11 generalised).
 //  k_energy_sum   E = sum_i a_i <P_i> (Eq. 2) with Neumaier compensation in FP64.
@@ -28,11 +29,6 @@ template <>
 struct Eps<float> {
   static constexpr float v = 1.1920929e-7f;
 };
-
-template <class R>
-__device__ __forceinline__ R shfl_x(R v, int o, int w) {
-  return __shfl_xor_sync(0xffffffffu, v, o, w);
-}
 
 // ------------------------------------------------------------------------- reset
 template <class R>
@@ -137,10 +133,13 @@ __device__ void block_gemm(int Mdim, int Ndim, int K, const GemmTerm<R>* terms, 
 // Shared-memory plan of k_circuit for bond cap chi (mmax = 2 chi), NT threads:
 //   [head]  U (16 complex double), U in R, FP64 reduction slots, misc ints
 //   [svd]   dd, ee, b (2 mmax), b2 (2 mmax), tauL, tauR, sig, lo, hi, coef (mmax each),
-//           cnt, xs (NT each)
-//   [W]     k x p real singular vectors of the bidiagonal (if it fits)
-//   [T]     (r + 1) x p complex, the tall orientation of M' (if it fits)
-// Anything that does not fit lives in the slot's global workspace (L2 resident).
+//           cnt, xs, bisection grid (NT each), iteration table (chi)
+//   [W]     chi rows of real singular vectors of the bidiagonal (stride ldw) and a
+//           chi x chi Gram area
+//   [T]     (mmax + 16) x mmax complex: the tall orientation of M', later the tiles of
+//           the site-update GEMM
+// When W and T do not both fit they live in the slot's global workspace (L2
+// resident) and only the GEMM tiles stay in shared memory.
 // Algorithmic real flops of one gate step, counted as the textbook dense algorithms:
 // contraction theta = B_n B_{n+1} (2 rl x rm x 2 rr complex MACs), the 4x4 gate on
 // (i, j), Golub-Reinsch SVD of the (m x n) complex M' computing singular values and
