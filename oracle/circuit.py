@@ -10,7 +10,7 @@ Paper passages followed:
   * Sec. III-A: single-qubit gates are absorbed into two-qubit gates by gate fusion,
     and two-qubit gates act on nearest neighbours (bond n = sites n, n+1).
 
-Readings, for exp(-i phi P / 2) with support S = {q : P_q != I},
+Readings where the paper does not draw the circuit, for exp(-i phi P / 2) with support S = {q : P_q != I},
 lo = min S, hi = max S:
   * basis change B_q = H for X, Rx(pi/2) = exp(-i pi X / 4) for Y, none for Z, so
     that B_q P_q B_q^+ = Z;

@@ -16,7 +16,7 @@ Paper passages followed (Sec. III-A):
   * Eq. (11) generalised to Pauli strings: <P> by a plain left-to-right
     contraction of transfer matrices over all sites, no shortcuts.
 
-Readings: keep k = min(chi, #{sigma > 1e-13 sigma_0}); the state is
+Readings where the paper leaves a choice: keep k = min(chi, #{sigma > 1e-13 sigma_0}); the state is
 never renormalised; energies are divided by <psi|psi>.
 
 Storage: B[k] has shape (r_{k-1}, 2, r_k); lam[k] holds the Schmidt numbers of the

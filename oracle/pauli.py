@@ -9,7 +9,7 @@ Paper passages followed:
     Pauli strings P in {I, X, Y, Z}^(x)n and E = sum_i a_i <P_i>.
   * Sec. III-C: H = sum_i a_i P_i with each P_i an n-qubit tensor product.
 
-Readings where the paper is silent (each stated again in the design doc):
+Readings where the paper is silent:
   * Integrals are in chemist order (pq|rs); with interleaved spin orbitals
     p = 2k + s the Hamiltonian is
         H = sum_{pq,s} h_pq a+_{ps} a_{qs}

@@ -9,7 +9,7 @@ Paper passages followed:
     product of exponentials, i.e. gates.
   * Sec. III-D: |Phi_0> is prepared by X gates on the first N_e qubits.
 
-Readings: spin-conserving, non-spin-adapted excitations with one
+Readings where the paper is silent: spin-conserving, non-spin-adapted excitations with one
 amplitude per i<j, a<b; tau = a+_a a_i (singles) and tau = a+_a a+_b a_i a_j
 (doubles); order: all singles by (i, a), then all doubles by ((i, j), (a, b)).
 Under Jordan-Wigner, tau - tau+ = i sum_k c_k P_k with real c_k and mutually

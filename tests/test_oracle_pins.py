@@ -142,7 +142,7 @@ def test_compiled_rotation_equals_definition(n):
         assert np.abs(fused - ref).max() < 1e-13
 
 
-def test_config1_two_site_gate_count():
+def test_uccsd_8q_two_site_gate_count():
     rc, rp, rs, exc = ucc.uccsd_rotations(8, 4)
     gates = circuit.compile_circuit(rc, rp, rs, np.zeros(len(exc)), 8)
     assert len(gates) == 1568
@@ -150,7 +150,7 @@ def test_config1_two_site_gate_count():
 
 # ---------------------------------------------------------------- c1 vs c2 and invariants
 @pytest.fixture(scope="module")
-def cfg1():
+def uccsd8():
     n, ne = 8, 4
     h, g = syn.random_integrals(4, 0)
     codes, coeffs = pauli.jordan_wigner_hamiltonian(h, g)
@@ -163,8 +163,8 @@ def cfg1():
                 theta=theta, psi=psi, st=st, dw=dw)
 
 
-def test_untruncated_mps_equals_statevector(cfg1):
-    c = cfg1
+def test_untruncated_mps_equals_statevector(uccsd8):
+    c = uccsd8
     assert c["dw"] < 1e-20
     psi2 = mps.to_statevector(c["st"])
     assert abs(np.vdot(c["psi"], psi2)) ** 2 >= 1 - 1e-12
@@ -174,8 +174,8 @@ def test_untruncated_mps_equals_statevector(cfg1):
     assert np.abs(ev1 - ev2).max() < 1e-12
 
 
-def test_invariants(cfg1):
-    c = cfg1
+def test_invariants(uccsd8):
+    c = uccsd8
     n = c["n"]
     assert abs(mps.norm2(c["st"]) - 1) < 1e-12
     _, ev = mps.energy(c["st"], c["codes"], c["coeffs"])
@@ -185,8 +185,8 @@ def test_invariants(cfg1):
     assert abs(np.vdot(psi, fock.sz2_operator(n) @ psi).real) < 1e-12
 
 
-def test_variational_bound(cfg1):
-    c = cfg1
+def test_variational_bound(uccsd8):
+    c = uccsd8
     Hf = fock.fock_hamiltonian(c["h"], c["g"])
     sec = fock.sector_indices(c["n"], c["ne"], 0)
     emin = np.linalg.eigvalsh(Hf[np.ix_(sec, sec)])[0]
