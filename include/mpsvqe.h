@@ -104,6 +104,13 @@ int circ_num_rotations(circ_t circ, int64_t* n_rot, int* n_params);
 int circ_get_rotations(circ_t circ, uint8_t* paulis, int32_t* param_idx, double* scale);
 int circ_num_gates(circ_t circ, int64_t* n_gates);
 int circ_export_gates(circ_t circ, const double* theta, int32_t* bond, double* U);
+/* Circuit-level variant (a gate-count optimisation on top of the paper's canonical
+ * list): consecutive gates on the same bond are multiplied into one, fixed gates next
+ * to a parametric gate are folded into it, identity products are dropped. The state
+ * is the same in exact arithmetic; truncated evaluations take fewer SVD steps and so
+ * differ slightly. Rewrites circ in place; n_gates (optional) receives the new count.
+ * Parameter-shift gradients stay exact (shifts act on the parametric gates only). */
+int circ_fuse_gates(circ_t circ, int64_t* n_gates);
 int circ_destroy(circ_t circ);
 
 /* ------------------------------------------------------------------ MPS state */

@@ -68,6 +68,7 @@ SIGNATURES = {
     "vqe_gradient": [_P, _P, _P, _P, _I, _P, _P],
     "mps_get_stats": [_P, ctypes.POINTER(MpsStats)],
     "mps_destroy": [_P],
+    "circ_fuse_gates": [_P, ctypes.POINTER(ctypes.c_int64)],
     "mps_estimate_bytes": [_I, _I, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_size_t)],
     "mps_apply_gates_noalloc": [_I, _I, _P, _P, _P, _P, _I64, _P, _P, _P, _PD],
     "mps_last_error": [],
@@ -227,6 +228,12 @@ def circ_get_rotations(circ):
     scale = np.zeros(nr.value)
     _check(lib.circ_get_rotations(circ, _ptr(paulis), _ptr(pidx), _ptr(scale)))
     return paulis, pidx, scale
+
+
+def circ_fuse_gates(circ):
+    n = ctypes.c_int64(0)
+    _check(load_library().circ_fuse_gates(circ, ctypes.byref(n)))
+    return int(n.value)
 
 
 def circ_num_gates(circ):

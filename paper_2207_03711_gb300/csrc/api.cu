@@ -507,6 +507,18 @@ int circ_export_gates(circ_t c, const double* theta, int32_t* bond, double* U) {
   return MPS_OK;
 }
 
+int circ_fuse_gates(circ_t c, int64_t* n_gates) {
+  if (!c) return fail(MPS_EINVAL, "circ_fuse_gates: null handle");
+  fuse_gates(&c->comp, &c->rot_param_gate);
+  c->uploaded = false;
+  dfree(c->d_gates);
+  dfree(c->d_mats);
+  c->d_gates = nullptr;
+  c->d_mats = nullptr;
+  if (n_gates) *n_gates = (int64_t)c->comp.gates.size();
+  return MPS_OK;
+}
+
 int circ_destroy(circ_t c) {
   delete c;
   return MPS_OK;
@@ -858,14 +870,9 @@ int vqe_gradient(mps_t m, circ_t c, ham_t h, const double* theta, int n_sel, con
     for (int i = 0; i < n_sel; ++i)
       if (sel[i] == R[k].param) si = i;
     if (si < 0) continue;
-    const int64_t g1 = k + 1 < R.size() ? c->comp.rot_first_gate[k + 1] : (int64_t)Gs.size();
-    int64_t pk = -1;
-    for (int64_t g = c->comp.rot_first_gate[k]; g < g1; ++g)
-      if (Gs[g].param >= 0) {
-        pk = g;
-        break;
-      }
-    if (pk < 0) return fail(MPS_EINVAL, "vqe_gradient: rotation without a parametric gate");
+    const int64_t pk = c->rot_param_gate[k];
+    if (pk < 0 || pk >= (int64_t)Gs.size() || Gs[pk].param != R[k].param)
+      return fail(MPS_EINVAL, "vqe_gradient: rotation without a parametric gate");
     tg.push_back({si, pk, R[k].scale});
   }
   for (int i = 0; i < n_sel; ++i) grad[i] = 0.0;

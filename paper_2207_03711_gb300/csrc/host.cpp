@@ -366,6 +366,90 @@ void compile_rotations(int n, const std::vector<Rotation>& rots, Compiled* out) 
   }
 }
 
+void fuse_gates(Compiled* c, std::vector<int64_t>* param_gate) {
+  const std::vector<GateRec>& G = c->gates;
+  const std::vector<cd>& Mv = c->mats;
+  auto get = [&](int32_t id) {
+    M4 m;
+    std::copy(Mv.begin() + 16 * (size_t)id, Mv.begin() + 16 * (size_t)id + 16, m.begin());
+    return m;
+  };
+  auto is_identity = [](const M4& m) {
+    for (int i = 0; i < 16; ++i)
+      if (std::abs(m[i] - cd((i % 5) == 0 ? 1.0 : 0.0)) > 1e-13) return false;
+    return true;
+  };
+  struct Item {
+    bool parametric;
+    M4 pre, post;  // fixed gate: pre only
+    GateRec rec;
+    int64_t rot;
+  };
+  const size_t nrot = c->rotations.size();
+  std::vector<int64_t> owner(G.size(), 0);
+  for (size_t r = 0; r < nrot; ++r) {
+    const int64_t e = r + 1 < nrot ? c->rot_first_gate[r + 1] : (int64_t)G.size();
+    for (int64_t g = c->rot_first_gate[r]; g < e; ++g) owner[g] = (int64_t)r;
+  }
+  std::vector<Item> out;
+  for (size_t g = 0; g < G.size(); ++g) {
+    Item it;
+    it.parametric = G[g].param >= 0;
+    it.pre = get(G[g].m0);
+    if (it.parametric) it.post = get(G[g].m1);
+    it.rec = G[g];
+    it.rot = owner[g];
+    if (!out.empty() && out.back().rec.bond == it.rec.bond) {
+      Item& h = out.back();
+      if (!h.parametric && !it.parametric) {  // fixed after fixed: one product
+        const M4 p = mm(it.pre, h.pre);
+        if (is_identity(p))
+          out.pop_back();
+        else
+          h.pre = p;
+        continue;
+      }
+      if (!h.parametric && it.parametric) {  // U (m1 Rz m0) after F: m0 <- m0 F
+        it.pre = mm(it.pre, h.pre);
+        out.back() = it;
+        continue;
+      }
+      if (h.parametric && !it.parametric) {  // F after U: m1 <- F m1
+        h.post = mm(it.pre, h.post);
+        continue;
+      }
+    }
+    out.push_back(it);
+  }
+  std::vector<cd> mats;
+  MatTable tab;
+  tab.mats = &mats;
+  std::vector<GateRec> gates;
+  gates.reserve(out.size());
+  param_gate->assign(nrot, -1);
+  std::vector<int64_t> first(nrot, (int64_t)out.size());
+  for (size_t i = 0; i < out.size(); ++i) {
+    GateRec rec = out[i].rec;
+    rec.m0 = tab.add(out[i].pre);
+    if (out[i].parametric) {
+      rec.m1 = tab.add(out[i].post);
+      (*param_gate)[out[i].rot] = (int64_t)i;
+    } else {
+      rec.param = -1;
+      rec.m1 = -1;
+    }
+    first[out[i].rot] = std::min(first[out[i].rot], (int64_t)i);
+    gates.push_back(rec);
+  }
+  // owners are non-decreasing along the list; a rotation without gates of its own
+  // starts where the next one does
+  for (size_t r = nrot; r-- > 0;)
+    if (r + 1 < nrot) first[r] = std::min(first[r], first[r + 1]);
+  c->gates = std::move(gates);
+  c->mats = std::move(mats);
+  c->rot_first_gate = std::move(first);
+}
+
 void gate_matrix(const Compiled& c, const GateRec& g, const double* theta, cd* U) {
   M4 a;
   std::copy(c.mats.begin() + 16 * (size_t)g.m0, c.mats.begin() + 16 * (size_t)g.m0 + 16, a.begin());

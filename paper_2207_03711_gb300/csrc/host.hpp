@@ -96,6 +96,14 @@ struct Compiled {
   std::vector<int64_t> rot_first_gate;  // first gate index of each rotation
 };
 void compile_rotations(int n, const std::vector<Rotation>& rots, Compiled* out);
+// Circuit-level variant (not the paper's canonical list): consecutive gates on the same
+// bond are multiplied into one, a fixed gate next to a parametric gate on the same bond
+// is folded into its pre or post matrix, and products equal to the identity are
+// dropped, so that the neighbours of a dropped pair meet in turn. The state is the
+// same in exact arithmetic; truncated runs take fewer SVD steps. param_gate receives
+// the index of each rotation's parametric gate (-1 if it has none); rot_first_gate is
+// rewritten to the first gate that carries each rotation's work.
+void fuse_gates(Compiled* c, std::vector<int64_t>* param_gate);
 // Host evaluation of a gate matrix for a given theta (inspection only).
 void gate_matrix(const Compiled& c, const GateRec& g, const double* theta, cd* U);
 

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import paper_2207_03711_gb300 as G
-from oracle import circuit, pauli, ucc
+from oracle import circuit, pauli, sv, ucc
 from paper_2207_03711_gb300 import synthetic as syn
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -138,3 +138,23 @@ def test_estimate_bytes_host_only():
     assert base >= 8 * sum(caps[k] * 2 * caps[k + 1] for k in range(12))
     with pytest.raises(G.MpsError):
         G.mps_estimate_bytes(12, 0, G.MPS_MIXED, 1)
+
+
+def test_fused_gate_list_is_the_same_circuit():
+    """circ_fuse_gates (a circuit-level variant): fewer gates, the same unitary. Checked
+    by applying both gate lists exactly to a statevector and against the oracle's
+    product of Pauli exponentials (no GPU)."""
+    n, ne = 8, 4
+    C = G.circ_uccsd(n, ne)
+    theta = syn.random_amplitudes(C.n_params, 3) * 5
+    b0, U0 = G.circ_export_gates(C, theta)
+    ng = G.circ_fuse_gates(C)
+    b1, U1 = G.circ_export_gates(C, theta)
+    assert ng == len(b1) < len(b0)
+    rc, rp, rs, _ = ucc.uccsd_rotations(n, ne)
+    ref = sv.run_ansatz(n, ne, rc, rp, rs, theta)
+    for bonds, Us in ((b0, U0), (b1, U1)):
+        psi = sv.hf_state(n, ne)
+        for b, U in zip(bonds, Us):
+            psi = circuit.apply_two_site_sv(psi, int(b), U, n)
+        assert np.abs(psi - ref).max() <= 1e-12

@@ -377,3 +377,25 @@ def test_vqe_loop_reaches_sector_ground_state():
     assert e >= e0 - 1e-9                      # variational bound
     assert e - e0 <= 1e-8
     assert hist[-1][1] <= hist[0][1]
+
+
+def test_fused_circuit_variant():
+    """The fused gate list (circ_fuse_gates) is the same circuit: untruncated FP64
+    energies and parameter-shift gradients equal the canonical list's and the oracle."""
+    n, ne, chi = 8, 4, 16
+    h, g = syn.random_integrals(4, 0)
+    codes, coeffs = pauli.jordan_wigner_hamiltonian(h, g)
+    rc, rp, rs, _ = ucc.uccsd_rotations(n, ne)
+    H = G.ham_jw_from_integrals(h, g)
+    C0, C1 = G.circ_uccsd(n, ne), G.circ_uccsd(n, ne)
+    assert G.circ_fuse_gates(C1) < G.circ_num_gates(C0)
+    theta = syn.random_amplitudes(C0.n_params, 0)
+    e_sv = sv.energy(sv.run_ansatz(n, ne, rc, rp, rs, theta), codes, coeffs)[0]
+    M = G.mps_create(n, chi, G.MPS_FP64, n_slots=9)
+    e0 = G.vqe_energy(M, C0, H, theta)
+    e1 = G.vqe_energy(M, C1, H, theta)
+    assert abs(e0 - e_sv) <= FP64_E_TOL and abs(e1 - e_sv) <= FP64_E_TOL
+    sel = [0, 5, C0.n_params - 1]
+    g0 = G.vqe_gradient(M, C0, H, theta, sel)
+    g1 = G.vqe_gradient(M, C1, H, theta, sel)
+    assert np.abs(g0 - g1).max() <= 1e-9
