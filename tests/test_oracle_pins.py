@@ -57,7 +57,7 @@ def test_h2_has_15_strings():
         assert len(codes) == 15
 
 
-def test_config_string_counts():
+def test_string_counts_8q_and_24q():
     h, g = syn.random_integrals(4, 0)
     assert len(pauli.jordan_wigner_hamiltonian(h, g)[0]) == 361
 
@@ -301,3 +301,49 @@ def test_planted_basis_change_error_is_caught(monkeypatch):
     monkeypatch.setattr(circuit, "RX90", circuit.RX90.conj().T)
     with pytest.raises(AssertionError):
         test_compiled_rotation_equals_definition(4)
+
+
+def _fold_single_qubit_gates(native):
+    """Fold every single-qubit gate into the next two-qubit gate touching its qubit (the
+    previous one if none follows); two-qubit gates stay separate."""
+    twoq = [i for i, g in enumerate(native) if g[0] == "2q"]
+    mats = {i: native[i][2].copy() for i in twoq}
+    for i, g in enumerate(native):
+        if g[0] != "1q":
+            continue
+        _, q, u = g
+        nxt = [j for j in twoq if j > i and native[j][1] in (q, q - 1)]
+        prv = [j for j in twoq if j < i and native[j][1] in (q, q - 1)]
+        j = nxt[0] if nxt else prv[-1]
+        b = native[j][1]
+        op = np.kron(u, circuit.I2) if b == q else np.kron(circuit.I2, u)
+        mats[j] = mats[j] @ op if nxt else op @ mats[j]
+    return [(native[j][1], mats[j]) for j in twoq]
+
+
+def test_single_qubit_fusion_keeps_truncated_result():
+    """Single-qubit unitaries never change Schmidt values, so folding them into two-qubit
+    gates leaves a truncated evolution unchanged (lambda on every bond, <P>)."""
+    n, chi = 8, 3
+    rng = np.random.default_rng(11)
+    st_a = mps.random_canonical(n, syn.full_ranks(n, chi), syn.random_mps_gaussians(n, syn.full_ranks(n, chi), 2))
+    st_b = st_a.copy()
+    codes = rng.integers(0, 4, size=(6, n)).astype(np.uint8)
+    codes[:, 2] = 1                                   # every string has support
+    for code in codes:
+        phi = rng.uniform(-1, 1)
+        native = circuit.native_gates(code, phi)
+        for g in native:
+            if g[0] == "1q":
+                _, q, u = g
+                st_a.B[q] = np.einsum("st,atb->asb", u, st_a.B[q])
+            else:
+                mps.apply_two_site(st_a, g[1], g[2], chi)
+        for b, U in _fold_single_qubit_gates(native):
+            mps.apply_two_site(st_b, b, U, chi)
+    for la, lb in zip(st_a.lam, st_b.lam):
+        assert len(la) == len(lb) and np.abs(la - lb).max() <= 1e-10
+    probe = rng.integers(0, 4, size=(20, n)).astype(np.uint8)
+    ea = np.array([mps.expect_string(st_a, c) for c in probe])
+    eb = np.array([mps.expect_string(st_b, c) for c in probe])
+    assert np.abs(ea - eb).max() <= 1e-10
