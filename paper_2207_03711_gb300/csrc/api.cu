@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -31,16 +32,33 @@ int cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
   } while (0)
 
-template <class T>
-int dalloc(T** p, size_t count) {
+// Every device allocation of the library goes through dev_alloc. Host-side fault
+// injection for tests: with MPS_FAULT_ALLOC_AFTER=k in the environment, the
+// allocations of one mps_create (or of one measurement-buffer set-up) after the
+// first k fail with MPS_ENOMEM, without touching the device.
+thread_local long g_alloc_count = 0;
+void reset_alloc_count() { g_alloc_count = 0; }
+int dev_alloc(void** p, size_t bytes, const char* what) {
   *p = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (const char* env = std::getenv("MPS_FAULT_ALLOC_AFTER")) {
+    if (g_alloc_count++ >= std::atol(env))
+      return fail(MPS_ENOMEM, std::string(what) + ": device allocation failed (injected fault)");
+  }
+  cudaError_t e = cudaMalloc(p, bytes == 0 ? 1 : bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(MPS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    *p = nullptr;
+    return fail(MPS_ENOMEM, std::string(what) + ": cudaMalloc: " + cudaGetErrorString(e));
   }
   return MPS_OK;
+}
+
+template <class T>
+int dalloc(T** p, size_t count) {
+  void* q = nullptr;
+  const int rc = dev_alloc(&q, (count == 0 ? 1 : count) * sizeof(T), "device buffer");
+  *p = (T*)q;
+  return rc;
 }
 #define TRY(call)              \
   do {                         \
@@ -238,11 +256,12 @@ static int ensure_theta(mps_s* m, size_t count) {
 
 static int ensure_meas(mps_s* m, int32_t nodes, int64_t terms) {
   const size_t chi2 = (size_t)m->chi * m->chi;
+  reset_alloc_count();
   if (!m->w.R) {
     void* p;
-    CU(cudaMalloc(&p, (size_t)(m->n + 1) * chi2 * m->es));
+    TRY(dev_alloc(&p, (size_t)(m->n + 1) * chi2 * m->es, "right environments"));
     m->w.R = p;
-    CU(cudaMalloc(&p, (size_t)m->dm.slot_elems * m->es));
+    TRY(dev_alloc(&p, (size_t)m->dm.slot_elems * m->es, "B-hat"));
     m->w.Bhat = p;
   }
   if (nodes > m->w_nodes) {
@@ -252,11 +271,11 @@ static int ensure_meas(mps_s* m, int32_t nodes, int64_t terms) {
     m->w.L[0] = m->w.L[1] = m->w.T = nullptr;
     m->w_nodes = 0;
     void* p;
-    if (cudaMalloc(&p, (size_t)nodes * chi2 * m->es) != cudaSuccess) return fail(MPS_ENOMEM, "env buffer");
+    TRY(dev_alloc(&p, (size_t)nodes * chi2 * m->es, "environment buffer"));
     m->w.L[0] = p;
-    if (cudaMalloc(&p, (size_t)nodes * chi2 * m->es) != cudaSuccess) return fail(MPS_ENOMEM, "env buffer");
+    TRY(dev_alloc(&p, (size_t)nodes * chi2 * m->es, "environment buffer"));
     m->w.L[1] = p;
-    if (cudaMalloc(&p, (size_t)nodes * 2 * chi2 * m->es) != cudaSuccess) return fail(MPS_ENOMEM, "T buffer");
+    TRY(dev_alloc(&p, (size_t)nodes * 2 * chi2 * m->es, "T buffer"));
     m->w.T = p;
     m->w_nodes = nodes;
   }
@@ -562,6 +581,7 @@ int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_str
   if (chi < 1 || chi > 128) return fail(MPS_EINVAL, "mps_create: chi out of [1, 128]");
   if (precision != MPS_FP64 && precision != MPS_MIXED) return fail(MPS_EINVAL, "mps_create: bad precision");
   if (n_slots < 1 || n_slots > 4096) return fail(MPS_EINVAL, "mps_create: n_slots out of [1, 4096]");
+  reset_alloc_count();
   auto m = std::make_unique<mps_s>();
   m->n = n_qubits;
   m->chi = chi;
@@ -589,15 +609,15 @@ int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_str
   d.slot_elems = off;
   const size_t mm = 2 * (size_t)chi;
   void* p;
-  if (cudaMalloc(&p, (size_t)n_slots * off * m->es) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: B"); }
+  TRY(dev_alloc(&p, (size_t)n_slots * off * m->es, "mps_create: B"));
   d.B = p;
   TRY(dalloc(&d.lam, (size_t)n_slots * (n - 1) * chi));
   TRY(dalloc(&d.rank, (size_t)n_slots * (n + 1)));
-  if (cudaMalloc(&p, (size_t)n_slots * mm * mm * m->es) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_M"); }
+  TRY(dev_alloc(&p, (size_t)n_slots * mm * mm * m->es, "mps_create: work_M"));
   d.work_M = p;
-  if (cudaMalloc(&p, (size_t)n_slots * mm * (mm + 16) * m->es) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_X"); }
+  TRY(dev_alloc(&p, (size_t)n_slots * mm * (mm + 16) * m->es, "mps_create: work_X"));
   d.work_X = p;
-  if (cudaMalloc(&p, (size_t)n_slots * 16 * chi * chi * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return fail(MPS_ENOMEM, "mps_create: work_S"); }
+  TRY(dev_alloc(&p, (size_t)n_slots * 16 * chi * chi * sizeof(double), "mps_create: work_S"));
   d.work_S = p;
   TRY(dalloc(&d.dw, n_slots));
   TRY(dalloc(&d.stat, (size_t)n_slots * 4));

@@ -6,7 +6,8 @@ so the gate chains of all requests in flight run side by side on the device (one
 block, i.e. one SM, per evaluation slot); a request that finishes releases its memory and
 the loop admits the next ones that fit (first fit in arrival order). Every result is
 computed by the same deterministic kernels as a lone call, so it does not depend on what
-else is in flight. Latencies (submit to result) give p50/p99 beside the throughput.
+else is in flight. A request can be cancelled (Future.cancel) until it starts running.
+Latencies (submit to result) give p50/p99 beside the throughput.
 
 The host objects of a request (Jordan-Wigner Hamiltonian with its prefix trie, compiled
 circuit) are built at submission, because the device-memory estimate needs their sizes.
@@ -117,6 +118,8 @@ class Server:
                     if self._closed and not self._queue:
                         return
                     picked = []
+                    for it in [q for q in self._queue if q.future.cancelled()]:
+                        self._queue.remove(it)          # cancelled while queued
                     if self.inflight < self.max_inflight:
                         room = self.budget - self.used
                         for it in list(self._queue):
@@ -155,6 +158,12 @@ class Server:
 
     def _run(self, it):
         it.t_start = time.perf_counter()
+        if not it.future.set_running_or_notify_cancel():   # cancelled after admission
+            with self._cv:
+                self.used -= it.need
+                self.inflight -= 1
+                self._cv.notify_all()
+            return
         try:
             value = self._execute(it)
             err = None

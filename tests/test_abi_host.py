@@ -158,3 +158,29 @@ def test_fused_gate_list_is_the_same_circuit():
         for b, U in zip(bonds, Us):
             psi = circuit.apply_two_site_sv(psi, int(b), U, n)
         assert np.abs(psi - ref).max() <= 1e-12
+
+
+def _injected_create(monkeypatch, after):
+    G.load_library()
+    monkeypatch.setenv("MPS_FAULT_ALLOC_AFTER", str(after))
+    with pytest.raises(G.MpsError) as e:
+        G.mps_create(8, 16, G.MPS_MIXED, n_slots=2)
+    assert e.value.code == G.MPS_ENOMEM
+    assert "injected" in str(e.value)
+
+
+def test_injected_allocation_failure_is_a_status_code(monkeypatch):
+    """Host-side fault injection (MPS_FAULT_ALLOC_AFTER=0): the first device allocation
+    of mps_create fails before any device call; the call returns MPS_ENOMEM."""
+    _injected_create(monkeypatch, 0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("after", [3, 7])
+def test_injected_allocation_failure_midway(monkeypatch, after):
+    """The same with real allocations before the injected failure: mps_create releases
+    what it took and reports MPS_ENOMEM; the next create without injection works."""
+    _injected_create(monkeypatch, after)
+    monkeypatch.delenv("MPS_FAULT_ALLOC_AFTER")
+    M = G.mps_create(8, 16, G.MPS_MIXED, n_slots=2)
+    M.close()

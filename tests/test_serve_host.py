@@ -73,3 +73,25 @@ def test_request_larger_than_budget_is_rejected():
         f = srv.submit(_req(0), need_bytes=101)
         with pytest.raises(MemoryError):
             f.result(timeout=5)
+
+
+def test_cancelled_request_never_runs():
+    gate = threading.Event()
+    ran = []
+
+    def run(req):
+        if req.tag == 0:
+            gate.wait(5)
+        ran.append(req.tag)
+        return req.tag
+
+    with Server(budget_bytes=100, max_inflight=4, run_fn=run) as srv:
+        f0 = srv.submit(_req(0), need_bytes=80)     # occupies the budget
+        f1 = srv.submit(_req(1), need_bytes=50)     # waits for memory
+        f2 = srv.submit(_req(2), need_bytes=50)
+        assert f1.cancel()                           # still queued: cancellable
+        gate.set()
+        assert f0.result(timeout=5) == 0 and f2.result(timeout=5) == 2
+        assert f1.cancelled()
+        st = srv.stats()
+    assert 1 not in ran and st["completed"] == 2
