@@ -7,6 +7,9 @@ optimal truncation), exact statevectors, finite differences, counts printed in
 the paper (Sec. III-D: 15 Pauli strings and 120 ansatz gates for H2), and a few
 planted mistakes that the pins must catch.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import scipy.linalg
@@ -49,12 +52,15 @@ def test_jw_equals_fock_space_hamiltonian(m):
     assert np.abs(Hj - Hf).max() < 1e-12
 
 
+H2 = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "h2_structure.json")))
+
+
 def test_h2_has_15_strings():
-    """Sec. III-D: the 4-qubit H2 Hamiltonian has 15 Pauli strings."""
+    """Sec. III-D: the 4-qubit H2 Hamiltonian has 15 Pauli strings (tests/golden)."""
     for seed in range(3):
         h, g = syn.h2_shaped_integrals(seed)
         codes, _ = pauli.jordan_wigner_hamiltonian(h, g)
-        assert len(codes) == 15
+        assert len(codes) == H2["pauli_strings"]
 
 
 def test_string_counts_8q_and_24q():
@@ -86,12 +92,16 @@ def test_uccsd_counts():
 
 
 def test_h2_double_is_120_native_gates():
-    """Sec. III-D: the H2 ansatz circuit has 120 gates (8 strings x 15)."""
+    """Sec. III-D: the H2 ansatz circuit has 120 gates, 8 exponentials x 15 (tests/golden);
+    the reference state takes 2 X gates."""
     ex = ("d", (0, 1, 2, 3))
-    codes, c = ucc.generator_strings(ex, 4)
-    assert len(codes) == 8
-    total = sum(len(circuit.native_gates(code, 0.3)) for code in codes)
-    assert total == 120
+    codes, c = ucc.generator_strings(ex, H2["n_qubits"])
+    assert len(codes) == H2["exponentials"]
+    per = [len(circuit.native_gates(code, 0.3)) for code in codes]
+    assert all(k == H2["gates_per_exponential"] for k in per)
+    assert sum(per) == H2["ansatz_gates"]
+    assert int(np.sum(sv.hf_state(H2["n_qubits"], H2["n_electrons"]) != 0)) == 1
+    assert H2["n_electrons"] == H2["reference_x_gates"]
 
 
 @pytest.mark.parametrize("n,ne", [(6, 2), (8, 4)])
