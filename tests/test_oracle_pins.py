@@ -8,6 +8,7 @@ the paper (Sec. III-D: 15 Pauli strings and 120 ansatz gates for H2), and a few
 planted mistakes that the pins must catch.
 """
 import json
+import math
 import os
 
 import numpy as np
@@ -357,3 +358,74 @@ def test_single_qubit_fusion_keeps_truncated_result():
     ea = np.array([mps.expect_string(st_a, c) for c in probe])
     eb = np.array([mps.expect_string(st_b, c) for c in probe])
     assert np.abs(ea - eb).max() <= 1e-10
+
+
+# ---------------------------------------------------------------- random canonical MPS
+@pytest.mark.parametrize("n,chi,seed", [(6, 4, 0), (8, 8, 1), (10, 5, 2), (9, 16, 3)])
+def test_random_canonical_has_exact_schmidt_numbers(n, chi, seed):
+    """random_canonical must return a right-canonical MPS of unit norm whose lambda on
+    every bond are the Schmidt numbers of the state it represents: the singular values
+    of the dense amplitudes reshaped across that bond (LAPACK SVD of the statevector,
+    a route that shares nothing with the QR + eigh construction)."""
+    ranks = syn.full_ranks(n, chi)
+    st = mps.random_canonical(n, ranks, syn.random_mps_gaussians(n, ranks, seed))
+    # every site right-canonical: sum_i B^i B^{i+} = I
+    for k, Bk in enumerate(st.B):
+        E = sum(Bk[:, i, :] @ Bk[:, i, :].conj().T for i in range(2))
+        assert np.abs(E - np.eye(Bk.shape[0])).max() < 1e-12, k
+    psi = mps.to_statevector(st)
+    assert abs(np.vdot(psi, psi).real - 1.0) < 1e-12
+    t = psi.reshape((2,) * n).transpose(tuple(range(n))[::-1]).reshape(-1)   # site 0 slowest
+    for b in range(n - 1):
+        s = np.linalg.svd(t.reshape(2 ** (b + 1), -1), compute_uv=False)
+        r = len(st.lam[b])
+        assert r == ranks[b]
+        assert np.abs(st.lam[b] - s[:r]).max() < 1e-12, b
+        assert np.all(s[r:] < 1e-12)                  # nothing beyond the stored rank
+        assert np.all(np.diff(st.lam[b]) <= 1e-15)    # descending
+
+
+class _SqrtDropped:
+    """numpy stand-in for the oracle module with sqrt replaced by the identity."""
+
+    def __getattr__(self, name):
+        return getattr(np, name)
+
+    @staticmethod
+    def sqrt(x):
+        return x
+
+
+def test_planted_squared_schmidt_numbers_are_caught(monkeypatch):
+    monkeypatch.setattr(mps, "np", _SqrtDropped())
+    with pytest.raises(AssertionError):
+        test_random_canonical_has_exact_schmidt_numbers(8, 8, 1)
+
+
+# ---------------------------------------------------------------- compensated summation
+def test_neumaier_sum_on_known_cancellations():
+    """Exact values: 1e16 + 1 - 1e16 = 1 (a plain sum gives 0), and 1 + 1e100 + 1 - 1e100
+    = 2 (Kahan's variant gives 0); the compensation term's sign decides both."""
+    assert sv.neumaier_sum([1e16, 1.0, -1e16]) == 1.0
+    assert sv.neumaier_sum([1.0, 1e100, 1.0, -1e100]) == 2.0
+    assert sv.neumaier_sum([]) == 0.0
+    assert sv.neumaier_sum([0.1] * 10) == math.fsum([0.1] * 10)
+
+
+def test_neumaier_sum_matches_correctly_rounded_sum():
+    """Against math.fsum (the correctly rounded sum) on long ill-conditioned series: the
+    compensated sum is within eps |S| + n eps^2 sum|x| of it (the textbook bound), while
+    the plain running sum misses by orders of magnitude more."""
+    rng = np.random.default_rng(7)
+    eps = np.finfo(float).eps
+    for trial in range(5):
+        x = rng.normal(size=20000) * 10.0 ** rng.uniform(-8, 8, size=20000)
+        x = np.concatenate([x, -x[rng.permutation(len(x))][:19990]])     # heavy cancellation
+        x = list(x[rng.permutation(len(x))])
+        exact = math.fsum(x)
+        bound = 2 * eps * abs(exact) + len(x) * eps ** 2 * sum(abs(v) for v in x)
+        assert abs(sv.neumaier_sum(x) - exact) <= bound
+        naive = 0.0
+        for v in x:
+            naive += v
+        assert abs(naive - exact) > 100 * bound     # the series really needs compensation
