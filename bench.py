@@ -3,14 +3,21 @@
 Workload (the 24-qubit configuration): 12 spatial orbitals / 24 qubits, 12
 electrons, seeded random 8-fold-symmetric integrals (29 737 Jordan-Wigner Pauli
 strings), UCCSD with 1818 excitations (14 112 Pauli rotations, 442 272 two-site
-gates), bond cap chi = 64, one energy evaluation per call (reset to Hartree-Fock,
-apply the circuit, evaluate every string, FP64 compensated sum). A step is one
-vqe_energy call in the mixed-precision mode.
+gates), bond cap chi = 64, mixed precision. A step is one energy evaluation
+(reset to Hartree-Fock, apply the whole circuit, evaluate every string, FP64
+compensated sum) with its own seeded theta, nothing skipped.
+
+One evaluation is a strictly serial chain of 442 272 truncated SVDs, so it runs on
+one SM. The K timed steps are therefore issued together, as one vqe_energy_batch
+call over K slots (one thread block, i.e. one SM, per evaluation), the way the
+serving loop runs independent requests; the W warm-up steps likewise. Each step's
+latency is the whole call; the throughput is K over it.
 
   value  energy evaluations per second with inputs resident on the device, from
          CUDA events recorded by the library on its stream around its kernels
-  e2e    the same metric through the C ABI call with host buffers (theta uploaded,
-         energy read back inside the timed region), from host wall-clock time
+  e2e    the same metric through the C ABI call with host buffers (thetas from
+         pinned host memory uploaded, energies read back inside the timed region),
+         from host wall-clock time
 
 `--impl reference` times the CPU oracle (the plain NumPy truncated-MPS code) on a
 bounded, stratified sample of the same workload instead.
@@ -36,15 +43,10 @@ WORKLOAD = {"workload": "uccsd_24q_12e_chi64_single_eval", "qubits": N_QUBITS, "
             "theta_seed": SEED, "evals_per_call": 1}
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of k_circuit in the 256-gate profile case
-# (ncu capture of the current kernel; None until one exists)
-TRAFFIC_PROFILE_CASE = 1.728256e6 + 0.090624e6
-
-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--serve", action="store_true",
@@ -174,51 +176,111 @@ def threads_used():
 
 
 # ------------------------------------------------------------------ reference arm
+def oracle_small_eval():
+    """One complete oracle evaluation of the 8-qubit, 4-electron, chi = 16 case (the
+    small configuration, exactly representable), timed end to end on the host: a
+    measured oracle rate beside the extrapolated 24-qubit one."""
+    from oracle import circuit, mps, pauli, ucc
+    from paper_2207_03711_gb300 import synthetic as syn
+    n, ne, chi = 8, 4, 16
+    h, g = syn.random_integrals(n // 2, SEED)
+    t0 = time.perf_counter()
+    codes, coeffs = pauli.jordan_wigner_hamiltonian(h, g)
+    rc, rp, rs, exc = ucc.uccsd_rotations(n, ne)
+    th = syn.random_amplitudes(len(exc), SEED)
+    st = mps.hf_mps(n, ne)
+    mps.apply_gates(st, circuit.compile_circuit(rc, rp, rs, th, n), chi)
+    e, _ = mps.energy(st, codes, coeffs)
+    dt = time.perf_counter() - t0
+    return {"workload": "uccsd_8q_4e_chi16_single_eval", "evals_per_s": 1.0 / dt, "seconds": dt,
+            "kind": "oracle", "energy_Ha": e, "pauli_terms": len(codes)}
+
+
 def run_reference(args):
+    """The oracle arm: each step times the oracle on a bounded, stratified sample of
+    one 24-qubit evaluation (see oracle_sample) and converts it to evaluations per
+    second by the extrapolation written there; ms_per_step is the measured wall time
+    of a sample step, evals_per_step the fraction of an evaluation it stands for."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     h, g = inputs()
-    vals = []
+    vals, steps_s, fracs = [], [], []
     sample = ""
+    budget = min(20.0, 150.0 / max(1, args.warmup + args.steps))
     for i in range(args.warmup + args.steps):
-        v, sample, est = oracle_sample(h, g, budget_s=min(20.0, 150.0 / max(1, args.warmup + args.steps)))
+        t0 = time.perf_counter()
+        v, sample, est = oracle_sample(h, g, budget_s=budget)
+        dt = time.perf_counter() - t0
         if i >= args.warmup:
             vals.append(v)
+            steps_s.append(dt)
+            fracs.append(dt / est)
     value = float(np.mean(vals))
     cores = threads_used()
     line = {"impl": "reference", "metric": "VQE energy evals/s", "value": value, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": 1e3 * float(np.mean(steps_s)), "evals_per_step": float(np.mean(fracs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
-            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle-extrapolated",
+                             "estimate": True, "sample": sample},
+            "oracle_full_small": oracle_small_eval(),
             "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ------------------------------------------------------------------ our arm
 def accuracy_probe(G):
-    """|dE| of both precisions against the oracle on the exactly representable 8-qubit
-    case (chi = 16 holds the state without truncation)."""
+    """|dE| of both precisions against the oracle on the exactly representable cases:
+    8 qubits at chi = 16 and 10 qubits at chi = 32 hold the state without truncation,
+    so the FP64 oracle's energy is the unique answer."""
     from oracle import circuit, mps, pauli, ucc
     from paper_2207_03711_gb300 import synthetic as syn
-    n, ne, chi = 8, 4, 16
-    h, g = syn.random_integrals(4, 0)
-    H = G.ham_jw_from_integrals(h, g)
-    C = G.circ_uccsd(n, ne)
-    th = syn.random_amplitudes(C.n_params, 0)
-    codes, coeffs = pauli.jordan_wigner_hamiltonian(h, g)
-    rc, rp, rs, _ = ucc.uccsd_rotations(n, ne)
-    st = mps.hf_mps(n, ne)
-    mps.apply_gates(st, circuit.compile_circuit(rc, rp, rs, th, n), chi)
-    e_ref = mps.energy(st, codes, coeffs)[0]
     out = {}
-    for name, prec in (("fp64", G.MPS_FP64), ("mixed", G.MPS_MIXED)):
-        M = G.mps_create(n, chi, prec)
-        out[f"abs_dE_Ha_{name}"] = abs(G.vqe_energy(M, C, H, th) - e_ref)
-        M.close()
-    out["case"] = "8 qubits, 4 electrons, chi=16 (untruncated), one evaluation vs the FP64 oracle"
+    for n, ne, chi in ((8, 4, 16), (10, 4, 32)):
+        h, g = syn.random_integrals(n // 2, 0)
+        H = G.ham_jw_from_integrals(h, g)
+        C = G.circ_uccsd(n, ne)
+        th = syn.random_amplitudes(C.n_params, 0)
+        codes, coeffs = pauli.jordan_wigner_hamiltonian(h, g)
+        rc, rp, rs, _ = ucc.uccsd_rotations(n, ne)
+        st = mps.hf_mps(n, ne)
+        mps.apply_gates(st, circuit.compile_circuit(rc, rp, rs, th, n), chi)
+        e_ref = mps.energy(st, codes, coeffs)[0]
+        for name, prec in (("fp64", G.MPS_FP64), ("mixed", G.MPS_MIXED)):
+            M = G.mps_create(n, chi, prec)
+            out[f"abs_dE_Ha_{name}_{n}q"] = abs(G.vqe_energy(M, C, H, th) - e_ref)
+            M.close()
+    out["cases"] = "8 qubits/4 electrons/chi 16 and 10 qubits/4 electrons/chi 32 (untruncated), vs the FP64 oracle"
+    return out
+
+
+def alu_peaks(torch):
+    """Measured CUDA-core peaks of this GPU, in this process: cuBLAS SGEMM and DGEMM at
+    8192^3 with TF32 disabled (best of 5, CUDA events). The gate engine runs on the
+    FP32 pipes, so SGEMM is its roofline denominator."""
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {}
+    try:
+        for name, dt, n, reps in (("fp32", torch.float32, 8192, 5), ("fp64", torch.float64, 4096, 3)):
+            a = torch.randn(n, n, device="cuda", dtype=dt)
+            b = torch.randn(n, n, device="cuda", dtype=dt)
+            torch.matmul(a, b)
+            best = 1e30
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                e1.synchronize()
+                best = min(best, e0.elapsed_time(e1) * 1e-3)
+            out[name + "_tflops"] = 2.0 * n ** 3 / best / 1e12
+            del a, b
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    out["how"] = "cuBLAS SGEMM 8192^3 and DGEMM 4096^3 (TF32 off), best of 5/3, CUDA events, this process"
     return out
 
 
@@ -231,9 +293,10 @@ def max_over_ranks(values, dist, device):
     return [float(v) for v in t.tolist()]
 
 
-def replica_rate(world, ms_per_step):
-    """Whole-job evaluations per second of `world` replicas, one evaluation each per step."""
-    return world * 1e3 / ms_per_step
+def replica_rate(world, evals_per_rank, seconds):
+    """Whole-job evaluations per second: every rank ran evals_per_rank evaluations and
+    the slowest rank took `seconds`."""
+    return world * evals_per_rank / seconds
 
 
 def run_ours(args):
@@ -254,99 +317,91 @@ def run_ours(args):
     h, g = inputs()
     H = G.ham_jw_from_integrals(h, g)
     C = G.circ_uccsd(N_QUBITS, N_ELEC)
-    theta = syn.random_amplitudes(C.n_params, SEED + rank)
     stream = torch.cuda.current_stream().cuda_stream
-    W = max(3, args.warmup)
-    # the warm-up evaluations run together as one batch with one evaluation per SM (at
-    # least W); their wall time gives the batched throughput reported beside the
-    # single-evaluation metric
+    K, W = args.steps, max(3, args.warmup)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    n_warm = max(W, n_sm)
-    M = G.mps_create(N_QUBITS, CHI, G.MPS_MIXED, n_slots=n_warm, cuda_stream=stream)
+    if K > n_sm:
+        raise SystemExit(f"--steps {K} exceeds the {n_sm} SMs: the timed steps run side by side, one SM each")
+    M = G.mps_create(N_QUBITS, CHI, G.MPS_MIXED, n_slots=max(K, W), cuda_stream=stream)
+    # thetas of the timed steps in pinned host memory (uploaded inside the timed call)
+    th_pinned = torch.empty((K, C.n_params), dtype=torch.float64, pin_memory=True)
+    th_host = th_pinned.numpy()
+    th_host[:] = np.stack([syn.random_amplitudes(C.n_params, SEED + 1000 * rank + i) for i in range(K)])
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
+    # warm-up: W evaluations issued together (also uploads the gate list and the trie)
+    tw0 = time.perf_counter()
+    G.vqe_energy_batch(M, C, H, np.stack([syn.random_amplitudes(C.n_params, 100 + i) for i in range(W)]),
+                       allow_noconv=True)
     torch.cuda.synchronize()
-    tb0 = time.perf_counter()
-    e_batch = G.vqe_energy_batch(M, C, H, np.stack([syn.random_amplitudes(C.n_params, 100 + i)
-                                                    for i in range(n_warm)]))
+    t_warm = time.perf_counter() - tw0
+    flush.fill_(1.0)          # L2 flushed before the timed call (outside the timing)
     torch.cuda.synchronize()
-    t_batch = time.perf_counter() - tb0
-    sampler = ClockSampler(local)
-    if rank == 0:
-        sampler.start()
-    dev_ms, wall_ms, energies, launches = [], [], [], []
-    flops, circ_ms = [], []
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.fill_(1.0)          # L2 flushed between timed steps (outside the timing)
-        torch.cuda.synchronize()
-        f0 = G.mps_get_stats(M)["alg_flops_total"]
-        t0 = time.perf_counter()
-        e = G.vqe_energy(M, C, H, theta)
-        t1 = time.perf_counter()
-        s = G.mps_get_stats(M)
-        energies.append(e)
-        wall_ms.append((t1 - t0) * 1e3)
-        dev_ms.append(s["ms_circuit"] + s["ms_measure"])
-        circ_ms.append(s["ms_circuit"])
-        flops.append(s["alg_flops_total"] - f0)
-        launches.append(int(s["kernel_launches"]))
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    t0 = time.perf_counter()
+    energies = G.vqe_energy_batch(M, C, H, th_host, allow_noconv=True)
+    t1 = time.perf_counter()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clocks = sampler.stop() if rank == 0 else {}
-    ms_dev, ms_wall = float(np.mean(dev_ms)), float(np.mean(wall_ms))
+    s = G.mps_get_stats(M)
+    dev_s = (s["ms_circuit"] + s["ms_measure"]) * 1e-3
+    wall_s = t1 - t0
+    circ_s = s["ms_circuit"] * 1e-3
+    flops = s["alg_flops_call"]
     if dist:
-        ms_dev, ms_wall = max_over_ranks([ms_dev, ms_wall], dist, "cuda")
+        dev_s, wall_s, circ_s = max_over_ranks([dev_s, wall_s, circ_s], dist, "cuda")
         if rank != 0:
             dist.destroy_process_group()
             return
-    s = G.mps_get_stats(M)
-    # dominant kernel: the gate engine (FP32 CUDA-core arithmetic, one block per evaluation)
-    peak = 152 * 128 * 2 * 2070e6 / 1e12                 # TFLOP/s, recipe unit counts x max clock
-    achieved = float(np.mean(flops)) / (float(np.mean(circ_ms)) * 1e-3) / 1e12
+    peaks = alu_peaks(torch)
+    # dominant kernel: the gate engine on the FP32 pipes, K thread blocks (one SM each)
+    achieved = flops / circ_s / 1e12
+    peak = peaks["fp32_tflops"]
     n_launch = (442272 + 16383) // 16384
-    value = replica_rate(world, ms_dev)
+    value = replica_rate(world, K, dev_s)
     cpu_val, cpu_sample, _ = oracle_sample(h, g)
     line = {
         "metric": "VQE energy evals/s", "value": value, "unit": "evals/s", "n_gpus": world,
-        "steps": args.steps, "warmup": W, "ms_per_step": ms_dev, "higher_is_better": True,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * dev_s / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-        "config": dict(WORKLOAD, precision="mixed (complex64 tensors, FP32 SVD, FP64 lambda/sums)",
-                       l2="flushed between timed steps (512 MB write)",
-                       warmup="max(W, SM count) evaluations issued as one batch on as many slots"),
+        "config": dict(WORKLOAD, precision="mixed (complex64 tensors, FP32 SVD, FP64 lambda and sums)",
+                       l2="flushed (512 MB write) before the timed call; the K steps run in that one call",
+                       steps_in_flight=K,
+                       warmup=f"{W} evaluations issued together, {t_warm:.1f} s wall"),
         "pauli_terms_per_s": value * 29737,
-        "latency_ms": {"p50": float(np.percentile(wall_ms, 50)), "p99": float(np.percentile(wall_ms, 99))},
-        "e2e": {"value": replica_rate(world, ms_wall), "unit": "evals/s", "h2d_bytes_per_step": 8 * C.n_params,
-                "d2h_bytes_per_step": 8 * 4 + 8 + 16},
-        "gpu_launches": int(np.mean(launches)),
+        "latency_s": {"p50": dev_s, "p99": dev_s,
+                      "note": "every step is in flight for the whole call and ends with it"},
+        "e2e": {"value": replica_rate(world, K, wall_s), "unit": "evals/s",
+                "h2d_bytes_per_step": 8 * C.n_params + N_QUBITS, "d2h_bytes_per_step": 8},
+        "gpu_launches": int(s["kernel_launches"]),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak,
-                     # DRAM bytes per launch: the ncu capture of the 256-gate profile case
-                     # (TRAFFIC_PROFILE_CASE bytes) scaled by the gates per launch; None
-                     # while no capture of the current kernel exists
-                     "traffic": (TRAFFIC_PROFILE_CASE / 256 * (442272 / n_launch)
-                                 if TRAFFIC_PROFILE_CASE is not None else None),
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the 256-gate "
-                                       "profile case, scaled to the mean gates per launch",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "measured: cuBLAS SGEMM in this process (FP32 CUDA cores)",
                      "kernel": "k_circuit<float,512>", "launches_per_step": n_launch,
-                     "frac_of_one_sm": achieved / (peak / 152),
-                     "note": "one thread block (one SM) per evaluation; peak is the whole GPU"},
-        "batched": {"evals": n_warm, "evals_per_s": n_warm / t_batch, "wall_s": t_batch,
-                    "pauli_terms_per_s": n_warm * 29737 / t_batch,
-                    "note": "the warm-up batch: one evaluation per SM in one launch per gate chunk, "
-                            "host wall time, distinct theta per evaluation",
-                    "energy_spread_Ha": float(np.max(e_batch) - np.min(e_batch))},
-        "cpu_baseline": {"value": cpu_val, "unit": "evals/s", "cores": threads_used(), "kind": "oracle",
-                         "sample": cpu_sample},
+                     "sms_busy": K * world,
+                     "frac_of_busy_sms": achieved / (peak * K / n_sm),
+                     "note": "achieved = algorithmic flops of all K evaluations' gate steps / circuit CUDA-event "
+                             "time; traffic null until an ncu capture of the current kernel exists"},
+        "alu_peaks_measured": peaks,
+        "cpu_baseline": {"value": cpu_val, "unit": "evals/s", "cores": threads_used(),
+                         "kind": "oracle-extrapolated", "estimate": True, "sample": cpu_sample},
+        "oracle_full_small": oracle_small_eval(),
         "clocks": clocks,
-        "energy_Ha": energies[-1],
-        "breakdown_ms": {"circuit": float(np.mean(circ_ms)), "measure": float(np.mean(dev_ms) - np.mean(circ_ms))},
-        "svd_fallbacks_total": int(s["n_fallback"]),
-        "discarded_weight": s["discarded_weight"],
+        "energy_Ha": {"min": float(np.min(energies)), "max": float(np.max(energies))},
+        "breakdown_ms": {"circuit": s["ms_circuit"], "measure": s["ms_measure"]},
+        "svd_fallbacks_slot0": int(s["n_fallback"]),
+        "svd_noconv": int(s["n_svd_noconv"]),
+        "discarded_weight_slot0": s["discarded_weight"],
         "accuracy": accuracy_probe(G),
     }
+    acc = line["accuracy"]
+    line["accuracy_Ha"] = max(acc["abs_dE_Ha_mixed_8q"], acc["abs_dE_Ha_mixed_10q"])
     print(json.dumps(line))
 
 

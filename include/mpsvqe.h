@@ -39,7 +39,9 @@ enum {
   MPS_ENOMEM = -2,   /* device or host allocation failed                          */
   MPS_ECUDA = -3,    /* a CUDA runtime call failed (message has the CUDA error)   */
   MPS_ETIMEOUT = -4, /* a bounded device-side wait ran out                        */
-  MPS_ENOCONV = -5   /* an SVD hit its sweep cap; results are still written       */
+  MPS_ENOCONV = -5,  /* an SVD hit its sweep cap; results are still written       */
+  MPS_ENONFINITE = -6 /* a gate's M' held a NaN or Inf: that gate was skipped and    */
+                      /* the state left as it was before it                          */
 };
 
 enum { MPS_FP64 = 0, MPS_MIXED = 1 };
@@ -118,9 +120,14 @@ int circ_destroy(circ_t circ);
 /* Allocate n_slots MPS states of n_qubits sites with bond cap chi (Eq. 6) on the
  * current device, each initialised to the all-zero product state. precision:
  * MPS_FP64 (complex128 tensors, FP64 SVD and contractions) or MPS_MIXED (complex64
- * tensors, FP32 contractions and SVD, FP64 Schmidt numbers and energy sums).
- * cuda_stream: a cudaStream_t (NULL = default stream). n_qubits in [2, 128],
- * chi in [1, 128], n_slots in [1, 4096]. Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA. */
+ * tensors, FP32 SVD with a compensated re-orthonormalisation of the kept singular
+ * vectors, FP32 gate contractions, environment contractions of bonds >= 32 on the
+ * tensor cores with compensated TF32 splits, FP64 Schmidt numbers and energy sums).
+ * cuda_stream: a cudaStream_t (NULL = default stream). Device memory is taken and
+ * returned stream-ordered on that stream. n_qubits in [2, 128], chi in [1, 256],
+ * n_slots in [1, 4096]; gates are applied at chi <= 128 only (the calls that apply
+ * gates return MPS_EINVAL above), larger chi serves states loaded with mps_set_state
+ * and measured. Errors: MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA. */
 int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_stream, mps_t* out);
 
 /* Sec. III-D: reset slot to the product state |occ_0 occ_1 ...> (bytes 0/1), all
@@ -133,6 +140,14 @@ int mps_reset(mps_t mps, int slot, const uint8_t* occ);
  * whose spectrum is numerically degenerate without a split; a gate that reaches the
  * cap is counted in n_svd_noconv and the call returns MPS_ENOCONV. */
 int mps_set_svd_params(mps_t mps, double cutoff, int max_sweeps);
+
+/* Memory of the trie measurement (Sec. III-C; no counterpart in the paper's text). The
+ * prefix trie of the strings is walked depth first in chunks of consecutive nodes of one
+ * level, each level keeping environment buffers (3 chi^2 complex entries per node) for
+ * one chunk: bytes bounds the sum of those buffers (at least 16 nodes per level).
+ * 0 restores the default, 4 GiB for chi <= 128 and 16 GiB above, which mps_estimate_bytes
+ * assumes. Results do not depend on the chunking. */
+int mps_set_meas_budget(mps_t mps, size_t bytes);
 
 /* Sec. III-A, Eqs. (7)-(10), for every gate of circ on slot 0 in order: contract
  * B_n B_{n+1} with the gate, scale rows by lambda_{n-1}, truncated SVD, B_{n+1} <- V,
@@ -149,7 +164,9 @@ int mps_apply_gates(mps_t mps, int64_t n_gates, const int32_t* bond, const doubl
 
 /* Eq. (11) generalised to Pauli strings (Sec. III-C): re[i] + i im[i] =
  * <psi|P_i|psi> / <psi|psi> on slot 0, by exact transfer-matrix contraction over
- * a prefix trie (shared left environments) and right identity environments. */
+ * a prefix trie (shared left environments, walked depth first in chunks) and right
+ * identity environments. Returns MPS_ETIMEOUT if a bounded wait inside a tensor-core
+ * GEMM ran out (mixed precision). */
 int mps_expect_paulis(mps_t mps, int64_t n_terms, const uint8_t* paulis, double* re, double* im);
 
 /* Checkpoint / inspection of one slot. ranks: n_qubits-1 bond ranks.
@@ -160,6 +177,11 @@ int mps_get_ranks(mps_t mps, int slot, int32_t* ranks);
 int mps_state_size(mps_t mps, int slot, int64_t* n_B, int64_t* n_lam);
 int mps_get_state(mps_t mps, int slot, double* B, double* lam);
 int mps_set_state(mps_t mps, int slot, const int32_t* ranks, const double* B, const double* lam);
+
+/* Eq. (2), Sec. III-C: E = sum_i a_i Re<P_i> / <psi|psi> of the state slot 0 holds now
+ * (no reset, no circuit), by the same trie measurement and Neumaier-compensated FP64
+ * sum in trie order as vqe_energy. */
+int mps_energy(mps_t mps, ham_t ham, double* energy);
 
 /* Sec. III-C/III-D energy evaluation on slot 0: reset to the reference
  * determinant of circ (circ_set_reference), apply circ with theta, evaluate every term
@@ -192,7 +214,8 @@ typedef struct {
   int32_t max_rank;        /* largest bond rank reached, slot 0                   */
   int32_t max_sweeps;      /* most bisection refinement passes of one gate        */
   int64_t n_gates;         /* gates applied per slot                               */
-  int64_t n_svd_noconv;    /* Jacobi fallbacks that hit their sweep cap            */
+  int64_t n_svd_noconv;    /* Jacobi fallbacks that hit their sweep cap, summed    */
+                           /* over the slots of the call                           */
   double ms_circuit;       /* CUDA-event time of the circuit kernels               */
   double ms_measure;       /* CUDA-event time of the measurement kernels           */
   int64_t kernel_launches; /* device kernels launched by the call                  */
@@ -205,6 +228,10 @@ typedef struct {
   double alg_flops_total;  /* slot-0 algorithmic real flops of all gate steps      */
                            /* since creation (dense contraction + Golub-Reinsch    */
                            /* SVD with right vectors + site update)                */
+  int64_t n_nonfinite;     /* gates skipped because M' held a NaN or Inf, summed   */
+                           /* over the slots of the call                           */
+  double alg_flops_call;   /* algorithmic real flops of this call's gate steps,    */
+                           /* summed over every slot the call ran                  */
 } mps_stats_t;
 int mps_get_stats(mps_t mps, mps_stats_t* stats);
 
@@ -217,34 +244,57 @@ int mps_estimate_bytes(int n_qubits, int chi, int precision, int n_slots, circ_t
 
 int mps_destroy(mps_t mps);
 
-/* Allocation-free gate application (the paper has no counterpart). Some callers
- * cannot let a library allocate device memory: code running inside a stream capture
- * that someone else owns, runtimes that hand out all device memory from their own
- * pools, or processes with a fixed memory budget. For them this entry point applies
- * n_gates two-site gates (Eqs. 7-10, mixed precision) to ONE MPS that lives entirely in
- * caller-owned DEVICE memory, and allocates nothing: its workspace is a 1 MiB
- * file-scope device array inside this library, present on every GPU that loads the
- * library until the process exits. Limits: chi <= 64, 2 <= n_qubits <= 128; larger
- * sizes return MPS_EINVAL.
+/* Allocation-free gate application. The paper has no counterpart: this entry point
+ * exists for callers that cannot have device memory allocated for them, such as
+ * runtimes that hand out all device memory from their own pools, processes held to a
+ * fixed device-memory budget, or code that may not call cudaMalloc or cudaFree at
+ * this point of its run (both can synchronise the device). For them it applies
+ * n_gates two-site gates (contraction with the 4x4 gate, row scaling by the Schmidt
+ * numbers of the left bond, truncated SVD, site update; mixed precision) to ONE MPS
+ * that lives entirely in caller-owned DEVICE memory, and allocates nothing: its
+ * workspace is a 1 MiB file-scope device array inside this library, present on every
+ * GPU that loads the library until the process exits. Limits: chi <= 64,
+ * 2 <= n_qubits <= 128; larger sizes return MPS_EINVAL.
  *   site_tensors: complex64 (float re, im) entries; site k starts at element
  *                 site_offsets[k] and has room for cap_{k-1} x 2 x cap_k entries,
  *                 cap_b = min(chi, 2^min(b+1, n-1-b)) (cap_{-1} = cap_{n-1} = 1); the
  *                 current tensor (r_{k-1}, 2, r_k) is packed row-major at its start.
  *   site_offsets: n_qubits int64 (device). lambdas: (n_qubits-1) x chi doubles, bond b
  *                 at b * chi (device). ranks: n_qubits+1 int32, ranks[0] = ranks[n] = 1,
- *                 ranks[b+1] = rank of bond b (device). All four are updated in place.
- *   bonds: n_gates int32 (device); gates: n_gates x 4 x 4 complex128, row index
- *          2 i_b + i_{b+1} (device). cuda_stream: stream for all work (NULL = default).
- *   discarded_weight: HOST pointer or NULL; receives the summed discarded fraction and
- *          makes the call wait for the stream.
+ *                 ranks[b+1] = rank of bond b, 1 <= ranks[b+1] <= cap_b (device). All
+ *                 four are updated in place.
+ *   bonds: n_gates int32 in [0, n_qubits-2] (device); gates: n_gates x 4 x 4
+ *          complex128, row index 2 i_b + i_{b+1} (device). cuda_stream: stream for all
+ *          work (NULL = default).
+ *   discarded_weight: HOST pointer or NULL. When given, it receives the summed
+ *          discarded fraction, the call waits for the stream, and problems that only
+ *          the device can see are reported: MPS_EINVAL for a bond or rank outside the
+ *          ranges above (the kernel checks them before indexing and stops there),
+ *          MPS_ENONFINITE for a gate skipped on a NaN or Inf, MPS_ENOCONV for a Jacobi
+ *          fallback that hit its sweep cap. With NULL the call does not wait and these
+ *          three are not reported (out-of-range bonds and ranks are still never used).
  * The first call on each device looks up the workspace address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture. Every call
- * shares the one workspace, so calls that overlap on the GPU (other streams or threads)
- * race and must be serialised by the caller. Returns MPS_EINVAL for null pointers or
- * sizes beyond the limits, MPS_ECUDA if a CUDA call fails. */
+ * shares the one workspace, and each call clears the accumulators it reads, so calls
+ * that overlap on the GPU (other streams or threads) race and must be serialised by the
+ * caller. Returns MPS_EINVAL for null pointers or sizes beyond the limits, MPS_ECUDA if
+ * a CUDA call fails. */
 int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors, const int64_t* site_offsets,
                             double* lambdas, int32_t* ranks, int64_t n_gates, const int32_t* bonds,
                             const double* gates, void* cuda_stream, double* discarded_weight);
+
+/* Real GEMM on the tensor cores (tcgen05, TMEM, TMA) with compensated TF32 splits:
+ * C = A . B^T with A (M x K), B (N x K), C (M x N), all FP32 row-major DEVICE arrays
+ * with leading dimensions lda, ldb >= K and ldc >= N. Each operand is split into
+ * hi = tf32(x) and lo = tf32(x - hi) and C is accumulated in FP32 as
+ * A_hi B_hi + A_hi B_lo + A_lo B_hi (relative error about 2^-21 of sum |a||b|). This
+ * is the contraction primitive of the environment sweeps (Eq. 11, Sec. III-C) in
+ * mixed precision, exported for tests and callers with their own operands. Takes
+ * temporary device memory for the split planes with cudaMallocAsync on cuda_stream and
+ * waits for the stream. Returns MPS_EINVAL for bad sizes or null pointers, MPS_ENOMEM,
+ * MPS_ECUDA, or MPS_ETIMEOUT if a bounded pipeline wait inside the kernel ran out. */
+int mps_tc_gemm_tf32x3(int M, int N, int K, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                       int64_t ldc, void* cuda_stream);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char* mps_last_error(void);

@@ -16,7 +16,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libmpsvqe.so")
 
-MPS_OK, MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA, MPS_ETIMEOUT, MPS_ENOCONV = 0, -1, -2, -3, -4, -5
+MPS_OK, MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA, MPS_ETIMEOUT, MPS_ENOCONV, MPS_ENONFINITE = 0, -1, -2, -3, -4, -5, -6
 MPS_FP64, MPS_MIXED = 0, 1
 
 # Every entry point of include/mpsvqe.h with its ctypes signature.
@@ -36,7 +36,8 @@ class MpsStats(ctypes.Structure):
                 ("n_svd_noconv", ctypes.c_int64), ("ms_circuit", ctypes.c_double),
                 ("ms_measure", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("cycles", ctypes.c_double * 7), ("n_fallback", ctypes.c_int64),
-                ("alg_flops_total", ctypes.c_double)]
+                ("alg_flops_total", ctypes.c_double), ("n_nonfinite", ctypes.c_int64),
+                ("alg_flops_call", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -56,6 +57,7 @@ SIGNATURES = {
     "mps_create": [_I, _I, _I, _I, _P, _PP],
     "mps_reset": [_P, _I, _P],
     "mps_set_svd_params": [_P, _D, _I],
+    "mps_set_meas_budget": [_P, ctypes.c_size_t],
     "mps_apply_circuit": [_P, _P, _P, _PD],
     "mps_apply_gates": [_P, _I64, _P, _P, _PD],
     "mps_expect_paulis": [_P, _I64, _P, _P, _P],
@@ -63,6 +65,7 @@ SIGNATURES = {
     "mps_state_size": [_P, _I, _PI64, _PI64],
     "mps_get_state": [_P, _I, _P, _P],
     "mps_set_state": [_P, _I, _P, _P, _P],
+    "mps_energy": [_P, _P, _PD],
     "vqe_energy": [_P, _P, _P, _P, _PD],
     "vqe_energy_batch": [_P, _P, _P, _I, _P, _P],
     "vqe_gradient": [_P, _P, _P, _P, _I, _P, _P],
@@ -71,6 +74,7 @@ SIGNATURES = {
     "circ_fuse_gates": [_P, ctypes.POINTER(ctypes.c_int64)],
     "mps_estimate_bytes": [_I, _I, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_size_t)],
     "mps_apply_gates_noalloc": [_I, _I, _P, _P, _P, _P, _I64, _P, _P, _P, _PD],
+    "mps_tc_gemm_tf32x3": [_I, _I, _I, _P, _I64, _P, _I64, _P, _I64, _P],
     "mps_last_error": [],
 }
 
@@ -270,6 +274,10 @@ def mps_set_svd_params(mps, cutoff, max_sweeps):
     _check(load_library().mps_set_svd_params(mps, cutoff, max_sweeps))
 
 
+def mps_set_meas_budget(mps, nbytes):
+    _check(load_library().mps_set_meas_budget(mps, int(nbytes)))
+
+
 def mps_apply_circuit(mps, circ, theta, allow_noconv=False):
     dw = ctypes.c_double()
     th = _f64(theta if theta is not None else np.zeros(max(circ.n_params, 1)))
@@ -330,7 +338,13 @@ def mps_set_state(mps, sites, lams, slot=0):
     _check(load_library().mps_set_state(mps, slot, _ptr(ranks), _ptr(B), _ptr(lam)))
 
 
-def vqe_energy(mps, circ, ham, theta, allow_noconv=True):
+def mps_energy(mps, ham):
+    e = ctypes.c_double()
+    _check(load_library().mps_energy(mps, ham, ctypes.byref(e)))
+    return e.value
+
+
+def vqe_energy(mps, circ, ham, theta, allow_noconv=False):
     e = ctypes.c_double()
     th = _f64(theta if theta is not None else np.zeros(max(circ.n_params, 1)))
     _check(load_library().vqe_energy(mps, circ, ham, _ptr(th), ctypes.byref(e)),
@@ -338,7 +352,7 @@ def vqe_energy(mps, circ, ham, theta, allow_noconv=True):
     return e.value
 
 
-def vqe_energy_batch(mps, circ, ham, thetas, allow_noconv=True):
+def vqe_energy_batch(mps, circ, ham, thetas, allow_noconv=False):
     th = _f64(thetas)
     nb = th.shape[0]
     out = np.zeros(nb)
@@ -347,7 +361,7 @@ def vqe_energy_batch(mps, circ, ham, thetas, allow_noconv=True):
     return out
 
 
-def vqe_gradient(mps, circ, ham, theta, sel, allow_noconv=True):
+def vqe_gradient(mps, circ, ham, theta, sel, allow_noconv=False):
     sel = np.ascontiguousarray(sel, dtype=np.int32)
     out = np.zeros(sel.shape[0])
     _check(load_library().vqe_gradient(mps, circ, ham, _ptr(_f64(theta)), sel.shape[0], _ptr(sel), _ptr(out)),
@@ -356,15 +370,22 @@ def vqe_gradient(mps, circ, ham, theta, sel, allow_noconv=True):
 
 
 def mps_apply_gates_noalloc(n_qubits, chi, site_tensors, site_offsets, lambdas, ranks, n_gates, bonds, gates,
-                            cuda_stream=0):
+                            cuda_stream=0, allow_noconv=False):
     """Device-pointer arguments (ints); returns the discarded weight. See include/mpsvqe.h."""
     dw = ctypes.c_double()
     _check(load_library().mps_apply_gates_noalloc(n_qubits, chi, ctypes.c_void_p(site_tensors),
                                                   ctypes.c_void_p(site_offsets), ctypes.c_void_p(lambdas),
                                                   ctypes.c_void_p(ranks), n_gates, ctypes.c_void_p(bonds),
                                                   ctypes.c_void_p(gates), ctypes.c_void_p(cuda_stream or None),
-                                                  ctypes.byref(dw)))
+                                                  ctypes.byref(dw)),
+           allow=(MPS_ENOCONV,) if allow_noconv else ())
     return dw.value
+
+
+def mps_tc_gemm_tf32x3(M, N, K, A, lda, B, ldb, C, ldc, cuda_stream=0):
+    """Device-pointer arguments (ints): C = A . B^T on the tensor cores. See include/mpsvqe.h."""
+    _check(load_library().mps_tc_gemm_tf32x3(M, N, K, ctypes.c_void_p(A), lda, ctypes.c_void_p(B), ldb,
+                                             ctypes.c_void_p(C), ldc, ctypes.c_void_p(cuda_stream or None)))
 
 
 def mps_get_stats(mps):

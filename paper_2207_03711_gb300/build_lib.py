@@ -1,7 +1,7 @@
 """Build the in-tree CUDA library libmpsvqe.so for sm_103a (GB300).
 
-Three translation units compiled in parallel (host.cpp with g++, kernels.cu and
-api.cu with nvcc), linked with nvcc into paper_2207_03711_gb300/libmpsvqe.so.
+Five translation units compiled in parallel (host.cpp with g++; kernels.cu, api.cu,
+tc_gemm.cu and env_tc.cu with nvcc), linked with nvcc into paper_2207_03711_gb300/libmpsvqe.so.
 The CUDA runtime is linked statically, so the library only needs the driver.
 """
 import os
@@ -44,7 +44,7 @@ def build(force=False, verbose=False):
         ["g++", "-O2", "-fPIC", "-std=c++17", "-Wall", *inc, "-c", os.path.join(CSRC, "host.cpp"),
          "-o", os.path.join(OBJ, "host.o")],
     ]
-    for name in ("kernels", "api"):
+    for name in ("kernels", "api", "tc_gemm", "env_tc"):
         jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *inc,
                      "-c", os.path.join(CSRC, name + ".cu"), "-o", os.path.join(OBJ, name + ".o")])
     with ThreadPoolExecutor(len(jobs)) as ex:
@@ -54,7 +54,8 @@ def build(force=False, verbose=False):
             sys.stdout.write(o)
     tmp = LIB + ".tmp"
     _run([nvcc, *ARCH, "-shared", "-o", tmp, os.path.join(OBJ, "host.o"), os.path.join(OBJ, "kernels.o"),
-          os.path.join(OBJ, "api.o")])
+          os.path.join(OBJ, "api.o"), os.path.join(OBJ, "tc_gemm.o"),
+          os.path.join(OBJ, "env_tc.o")])
     os.replace(tmp, LIB)
     return LIB
 

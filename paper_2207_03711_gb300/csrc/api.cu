@@ -11,12 +11,15 @@
 
 #include "../../include/mpsvqe.h"
 #include "host.hpp"
+#include "env_tc.cuh"
 #include "kernels.cuh"
 
 using namespace mpsvqe;
 
 namespace {
 constexpr double kHalfPi = 1.5707963267948966;
+constexpr int kMaxChi = 256;        // largest bond cap of a handle (measurement)
+constexpr int kMaxGateChi = 128;    // largest bond cap the gate engine applies gates at
 thread_local std::string g_err;
 
 int fail(int code, const std::string& msg) {
@@ -32,31 +35,34 @@ int cuda_fail(cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);          \
   } while (0)
 
-// Every device allocation of the library goes through dev_alloc. Host-side fault
-// injection for tests: with MPS_FAULT_ALLOC_AFTER=k in the environment, the
-// allocations of one mps_create (or of one measurement-buffer set-up) after the
-// first k fail with MPS_ENOMEM, without touching the device.
+// Every device allocation of the library goes through dev_alloc. Allocations are
+// stream-ordered (cudaMallocAsync / cudaFreeAsync from the device's memory pool) on the
+// stream of the handle that owns them, so creating or destroying one handle never waits
+// for work other handles have in flight on other streams (a plain cudaFree synchronises
+// the whole device). Host-side fault injection for tests: with MPS_FAULT_ALLOC_AFTER=k in
+// the environment, the allocations of one mps_create (or of one measurement-buffer
+// set-up) after the first k fail with MPS_ENOMEM, without touching the device.
 thread_local long g_alloc_count = 0;
 void reset_alloc_count() { g_alloc_count = 0; }
-int dev_alloc(void** p, size_t bytes, const char* what) {
+int dev_alloc(void** p, size_t bytes, const char* what, cudaStream_t st = nullptr) {
   *p = nullptr;
   if (const char* env = std::getenv("MPS_FAULT_ALLOC_AFTER")) {
     if (g_alloc_count++ >= std::atol(env))
       return fail(MPS_ENOMEM, std::string(what) + ": device allocation failed (injected fault)");
   }
-  cudaError_t e = cudaMalloc(p, bytes == 0 ? 1 : bytes);
+  cudaError_t e = cudaMallocAsync(p, bytes == 0 ? 1 : bytes, st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
-    return fail(MPS_ENOMEM, std::string(what) + ": cudaMalloc: " + cudaGetErrorString(e));
+    return fail(MPS_ENOMEM, std::string(what) + ": cudaMallocAsync: " + cudaGetErrorString(e));
   }
   return MPS_OK;
 }
 
 template <class T>
-int dalloc(T** p, size_t count) {
+int dalloc(T** p, size_t count, cudaStream_t st = nullptr) {
   void* q = nullptr;
-  const int rc = dev_alloc(&q, (count == 0 ? 1 : count) * sizeof(T), "device buffer");
+  const int rc = dev_alloc(&q, (count == 0 ? 1 : count) * sizeof(T), "device buffer", st);
   *p = (T*)q;
   return rc;
 }
@@ -66,8 +72,11 @@ int dalloc(T** p, size_t count) {
     if (r_ != MPS_OK) return r_; \
   } while (0)
 
-void dfree(void* p) {
-  if (p) cudaFree(p);
+// Every call of the library has finished its device work when it returns, so a buffer
+// is idle when its handle is destroyed and can go back to the pool in the order of any
+// stream; the legacy stream is used for the shared circuit and Hamiltonian tables.
+void dfree(void* p, cudaStream_t st = nullptr) {
+  if (p) cudaFreeAsync(p, st);
 }
 }  // namespace
 
@@ -118,8 +127,13 @@ struct mps_s {
   DevMPS dm{};
   int64_t* d_site_off = nullptr;
   MeasDev w{};
-  int32_t w_nodes = 0;
   int64_t w_terms = 0;
+  // chunked trie measurement: per level, environment buffers for up to lvl_cap[k] nodes
+  std::vector<void*> lvl_L, lvl_T;
+  std::vector<int32_t> lvl_cap;
+  size_t meas_budget = 0;          // 0: the default of meas_plan
+  EnvTc tc{};
+  size_t tc_floats = 0;
   double* d_theta = nullptr;
   size_t theta_cap = 0;
   uint8_t* d_occ = nullptr;
@@ -132,28 +146,29 @@ struct mps_s {
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   std::vector<double> h_out;
   ~mps_s() {
-    dfree(dm.B);
-    dfree(dm.lam);
-    dfree(dm.rank);
-    dfree(dm.work_M);
-    dfree(dm.work_X);
-    dfree(dm.work_S);
-    dfree(dm.dw);
-    dfree(dm.stat);
-    dfree(dm.prof);
-    dfree(d_site_off);
-    dfree(w.R);
-    dfree(w.Bhat);
-    dfree(w.L[0]);
-    dfree(w.L[1]);
-    dfree(w.T);
-    dfree(w.vals);
-    dfree(w.out);
-    dfree(d_theta);
-    dfree(d_occ);
-    dfree(d_start_gate);
-    dfree(d_shift_gate);
-    dfree(d_shift_val);
+    dfree(dm.B, st);
+    dfree(dm.lam, st);
+    dfree(dm.rank, st);
+    dfree(dm.work_M, st);
+    dfree(dm.work_X, st);
+    dfree(dm.work_S, st);
+    dfree(dm.dw, st);
+    dfree(dm.stat, st);
+    dfree(dm.prof, st);
+    dfree(d_site_off, st);
+    dfree(w.R, st);
+    dfree(w.Bhat, st);
+    for (void* p : lvl_L) dfree(p, st);
+    for (void* p : lvl_T) dfree(p, st);
+    dfree(tc.scratch, st);
+    dfree(tc.err, st);
+    dfree(w.vals, st);
+    dfree(w.out, st);
+    dfree(d_theta, st);
+    dfree(d_occ, st);
+    dfree(d_start_gate, st);
+    dfree(d_shift_gate, st);
+    dfree(d_shift_val, st);
     for (auto e : ev)
       if (e) cudaEventDestroy(e);
   }
@@ -246,48 +261,107 @@ static int upload_circ(circ_s* c) {
 
 static int ensure_theta(mps_s* m, size_t count) {
   if (count <= m->theta_cap) return MPS_OK;
-  dfree(m->d_theta);
+  dfree(m->d_theta, m->st);
   m->d_theta = nullptr;
   m->theta_cap = 0;
-  TRY(dalloc(&m->d_theta, count));
+  TRY(dalloc(&m->d_theta, count, m->st));
   m->theta_cap = count;
   return MPS_OK;
 }
 
-static int ensure_meas(mps_s* m, int32_t nodes, int64_t terms) {
+// Chunked measurement plan. The prefix trie is walked depth first in chunks of
+// consecutive nodes of one level, so only one chunk per level is live: level k keeps
+// environment buffers (L: chi^2, T: 2 chi^2 complex entries per node) for cap[k] nodes.
+// cap[k] = min(nodes of level k, U) with U set by a per-handle budget (4 GiB of level
+// buffers for chi <= 128, 16 GiB above) spread over the levels; in mixed precision the
+// tensor-core scratch holds tc_nodes nodes (about 1 GiB).
+constexpr int kTcMinDim = 32;     // levels with both bonds >= 32 use the tensor cores
+struct MeasPlan {
+  std::vector<int32_t> cap;
+  int tc_nodes = 0;
+  size_t level_bytes = 0, tc_bytes = 0;
+};
+static MeasPlan meas_plan(const Trie& t, int chi, size_t es, bool mixed, size_t budget = 0) {
+  MeasPlan p;
+  const size_t chi2 = (size_t)chi * chi, node_bytes = 3 * chi2 * es;
+  if (budget == 0) budget = (chi <= 128 ? size_t(4) : size_t(16)) << 30;
+  const size_t per_level = budget / (size_t)std::max(1, t.n_levels);
+  const int32_t U = (int32_t)std::max<size_t>(16, per_level / node_bytes);
+  p.cap.assign(t.n, 0);
+  int32_t cmax = 1;
+  for (int k = 0; k < t.n_levels; ++k) {
+    p.cap[k] = std::min(t.level_nodes[k], U);
+    cmax = std::max(cmax, p.cap[k]);
+    p.level_bytes += (size_t)p.cap[k] * node_bytes;
+  }
+  if (mixed && chi >= kTcMinDim) {
+    const size_t per_node = 96 * chi2;    // float planes and GEMM outputs per node
+    p.tc_nodes = (int)std::min<size_t>((size_t)cmax, std::max<size_t>(32, (size_t(1) << 30) / per_node));
+    p.tc_bytes = env_tc_scratch_floats(chi, p.tc_nodes) * sizeof(float) + 256;
+  }
+  return p;
+}
+
+static int ensure_meas(mps_s* m, ham_s* h) {
   const size_t chi2 = (size_t)m->chi * m->chi;
+  const int64_t terms = std::max<int64_t>(1, (int64_t)h->terms.size());
   reset_alloc_count();
   if (!m->w.R) {
     void* p;
-    TRY(dev_alloc(&p, (size_t)(m->n + 1) * chi2 * m->es, "right environments"));
+    TRY(dev_alloc(&p, (size_t)(m->n + 1) * chi2 * m->es, "right environments", m->st));
     m->w.R = p;
-    TRY(dev_alloc(&p, (size_t)m->dm.slot_elems * m->es, "B-hat"));
+    TRY(dev_alloc(&p, (size_t)m->dm.slot_elems * m->es, "B-hat", m->st));
     m->w.Bhat = p;
   }
-  if (nodes > m->w_nodes) {
-    dfree(m->w.L[0]);
-    dfree(m->w.L[1]);
-    dfree(m->w.T);
-    m->w.L[0] = m->w.L[1] = m->w.T = nullptr;
-    m->w_nodes = 0;
+  const MeasPlan plan = meas_plan(h->trie, m->chi, m->es, m->prec == MPS_MIXED, m->meas_budget);
+  m->lvl_L.resize(m->n, nullptr);
+  m->lvl_T.resize(m->n, nullptr);
+  m->lvl_cap.resize(m->n, 0);
+  for (int k = 0; k < m->n; ++k) {
+    if (plan.cap[k] <= m->lvl_cap[k]) continue;
+    dfree(m->lvl_L[k], m->st);
+    dfree(m->lvl_T[k], m->st);
+    m->lvl_L[k] = m->lvl_T[k] = nullptr;
+    m->lvl_cap[k] = 0;
+    TRY(dev_alloc(&m->lvl_L[k], (size_t)plan.cap[k] * chi2 * m->es, "environment buffer", m->st));
+    TRY(dev_alloc(&m->lvl_T[k], (size_t)plan.cap[k] * 2 * chi2 * m->es, "T buffer", m->st));
+    m->lvl_cap[k] = plan.cap[k];
+  }
+  if (plan.tc_nodes > m->tc.max_nodes) {
+    dfree(m->tc.scratch, m->st);
+    m->tc.scratch = nullptr;
+    m->tc.max_nodes = 0;
     void* p;
-    TRY(dev_alloc(&p, (size_t)nodes * chi2 * m->es, "environment buffer"));
-    m->w.L[0] = p;
-    TRY(dev_alloc(&p, (size_t)nodes * chi2 * m->es, "environment buffer"));
-    m->w.L[1] = p;
-    TRY(dev_alloc(&p, (size_t)nodes * 2 * chi2 * m->es, "T buffer"));
-    m->w.T = p;
-    m->w_nodes = nodes;
+    TRY(dev_alloc(&p, plan.tc_bytes, "tensor-core scratch", m->st));
+    m->tc.scratch = (float*)p;
+    if (!m->tc.err) TRY(dalloc(&m->tc.err, 1, m->st));
+    m->tc.chi = m->chi;
+    m->tc.max_nodes = plan.tc_nodes;
   }
   if (terms > m->w_terms) {
-    dfree(m->w.vals);
-    dfree(m->w.out);
+    dfree(m->w.vals, m->st);
+    dfree(m->w.out, m->st);
     m->w.vals = m->w.out = nullptr;
     m->w_terms = 0;
-    TRY(dalloc(&m->w.vals, (size_t)terms * 2));
-    TRY(dalloc(&m->w.out, 4 + (size_t)terms * 2));
+    TRY(dalloc(&m->w.vals, (size_t)terms * 2, m->st));
+    TRY(dalloc(&m->w.out, 4 + (size_t)terms * 2, m->st));
     m->w_terms = terms;
   }
+  return MPS_OK;
+}
+
+// Sum over slots [slot0, slot0 + count) of the algorithmic flops the gate engine has
+// counted since creation (profile word 7 of each slot, a double).
+static int sum_slot_flops(mps_s* m, int slot0, int count, double* total) {
+  std::vector<unsigned long long> pr((size_t)count * 8);
+  CU(cudaMemcpy(pr.data(), m->dm.prof + (size_t)slot0 * 8, pr.size() * 8, cudaMemcpyDeviceToHost));
+  double t = 0.0;
+  for (int s = 0; s < count; ++s) {
+    double f;
+    std::memcpy(&f, &pr[(size_t)s * 8 + 7], 8);
+    t += f;
+  }
+  *total = t;
   return MPS_OK;
 }
 
@@ -298,6 +372,9 @@ static int ensure_meas(mps_s* m, int32_t nodes, int64_t terms) {
 static int run_circuit(mps_s* m, circ_s* c, int slot0, int count, const double* thetas,
                        const int64_t* start = nullptr, const int64_t* shift_gate = nullptr,
                        const double* shift_phi = nullptr, int64_t g_end = -1) {
+  if (m->chi > kMaxGateChi)
+    return fail(MPS_EINVAL, "gate application supports bond caps up to 128; a handle with a larger chi can be "
+                            "loaded (mps_set_state) and measured");
   TRY(upload_circ(c));
   const int np = std::max(1, c->comp.n_params);
   TRY(ensure_theta(m, (size_t)count * np));
@@ -319,6 +396,8 @@ static int run_circuit(mps_s* m, circ_s* c, int slot0, int count, const double* 
     cd.shift_phi = m->d_shift_val;
   }
   const int64_t chunk = 16384;
+  double flops0 = 0.0, flops1 = 0.0;
+  TRY(sum_slot_flops(m, slot0, count, &flops0));
   CU(cudaEventRecord(m->ev[0], m->st));
   int launches = 0;
   for (int64_t g0 = g_begin; g0 < G; g0 += chunk) {
@@ -333,6 +412,8 @@ static int run_circuit(mps_s* m, circ_s* c, int slot0, int count, const double* 
   m->stats.ms_circuit += ms;
   m->stats.kernel_launches += launches;
   m->stats.n_gates = (int64_t)c->comp.gates.size();
+  TRY(sum_slot_flops(m, slot0, count, &flops1));
+  m->stats.alg_flops_call += flops1 - flops0;
   return MPS_OK;
 }
 
@@ -345,13 +426,8 @@ static int copy_slot(mps_s* m, int src, int dst) {
   const size_t nr = (size_t)m->n + 1;
   CU(cudaMemcpyAsync(m->dm.rank + dst * nr, m->dm.rank + src * nr, nr * 4, cudaMemcpyDeviceToDevice, m->st));
   CU(cudaMemcpyAsync(m->dm.dw + dst, m->dm.dw + src, 8, cudaMemcpyDeviceToDevice, m->st));
-  CU(cudaMemcpyAsync(m->dm.stat + 4 * dst, m->dm.stat + 4 * src, 16, cudaMemcpyDeviceToDevice, m->st));
-  return MPS_OK;
-}
-
-static int read_slot_stats(mps_s* m, int slot, double* dw, int* stat4) {
-  CU(cudaMemcpy(dw, m->dm.dw + slot, 8, cudaMemcpyDeviceToHost));
-  CU(cudaMemcpy(stat4, m->dm.stat + 4 * slot, 16, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpyAsync(m->dm.stat + kStatWords * dst, m->dm.stat + kStatWords * src, 4 * kStatWords,
+                     cudaMemcpyDeviceToDevice, m->st));
   return MPS_OK;
 }
 
@@ -362,45 +438,107 @@ static int upload_reset(mps_s* m, int slot0, int count, const uint8_t* occ_rows)
   return MPS_OK;
 }
 
+// Depth-first walk over the prefix trie in chunks (see meas_plan). Chunk [u0, u1) of
+// level k has its environments L in lvl_L[k]; T_j = L B_k^j goes to lvl_T[k], the
+// strings that close at level k are evaluated from it, and the children are built and
+// walked chunk by chunk. Mixed precision runs the contractions of levels whose bonds
+// are both >= kTcMinDim on the tensor cores (env_tc.cu), the others on the CUDA-core
+// tile kernels; both use the same buffer layouts.
+struct MeasWalk {
+  mps_s* m;
+  ham_s* h;
+  int slot;
+  std::vector<int> r;   // bond ranks of the slot, r[k] = left dimension of site k
+  int launches = 0;
+};
+
+static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
+  mps_s* m = c.m;
+  const Trie& t = c.h->trie;
+  const int U = u1 - u0, D = c.r[k], Dp = c.r[k + 1];
+  const size_t chi2 = (size_t)m->chi * m->chi;
+  void* L = m->lvl_L[k];
+  void* T = m->lvl_T[k];
+  const bool tc = m->prec == MPS_MIXED && m->tc.scratch && D >= kTcMinDim && Dp >= kTcMinDim;
+  if (tc) {
+    const Cx<float>* Bk = (const Cx<float>*)m->dm.B + (size_t)c.slot * m->dm.slot_elems + m->site_off[k];
+    CU(env_tc_site(m->tc, Bk, D, Dp, m->st));
+    ++c.launches;
+    for (int s0 = 0; s0 < U; s0 += m->tc.max_nodes) {
+      const int ns = std::min(m->tc.max_nodes, U - s0);
+      CU(env_tc_T(m->tc, (const Cx<float>*)L + (size_t)s0 * chi2, (Cx<float>*)T + (size_t)s0 * 2 * chi2, ns, D, Dp,
+                  m->st));
+      c.launches += 3;
+    }
+  } else {
+    CU(launch_env_T(m->dm, m->prec, c.slot, k, L, T, U, m->st));
+    ++c.launches;
+  }
+  // strings closing at level k on this chunk's nodes
+  const auto& cn = t.close_node[k];
+  const int64_t cs = std::lower_bound(cn.begin(), cn.end(), u0) - cn.begin();
+  const int64_t ce = std::lower_bound(cn.begin(), cn.end(), u1) - cn.begin();
+  if (ce > cs) {
+    CU(launch_env_close(m->dm, m->prec, c.slot, k, T, m->w.Bhat, c.h->d_cnode[k] + cs, c.h->d_cletter[k] + cs,
+                        c.h->d_cterm[k] + cs, (int)(ce - cs), u0, m->w.vals, m->st));
+    ++c.launches;
+  }
+  if (k + 1 >= t.n_levels || k + 1 >= m->n) return MPS_OK;
+  const auto& par = t.parent[k + 1];
+  int64_t a = std::lower_bound(par.begin(), par.end(), u0) - par.begin();
+  const int64_t c1 = std::lower_bound(par.begin(), par.end(), u1) - par.begin();
+  while (a < c1) {
+    int64_t b = a + 1;
+    while (b < c1 && b - a < m->lvl_cap[k + 1] && (!tc || par[b] - par[a] < m->tc.max_nodes)) ++b;
+    if (tc) {
+      CU(env_tc_children(m->tc, (const Cx<float>*)T, par[a] - u0, par[b - 1] - u0 + 1, D, Dp,
+                         c.h->d_parent[k + 1] + a, c.h->d_edge[k + 1] + a, (int)(b - a), u0,
+                         (Cx<float>*)m->lvl_L[k + 1], m->st));
+      c.launches += 3;
+    } else {
+      CU(launch_env_child(m->dm, m->prec, c.slot, k, T, c.h->d_parent[k + 1] + a, c.h->d_edge[k + 1] + a,
+                          (int)(b - a), u0, m->lvl_L[k + 1], m->st));
+      ++c.launches;
+    }
+    TRY(meas_chunk(c, k + 1, (int)a, (int)b));
+    a = b;
+  }
+  return MPS_OK;
+}
+
 // Evaluate all terms of h on one slot; out_host receives 4 + 2 T doubles.
 static int run_measure(mps_s* m, ham_s* h, int slot, double* out_host, bool terms = true) {
   TRY(upload_ham(h));
   const int64_t T = (int64_t)h->terms.size();
-  TRY(ensure_meas(m, std::max<int32_t>(1, h->trie.max_level_nodes), std::max<int64_t>(1, T)));
+  TRY(ensure_meas(m, h));
+  MeasWalk c{m, h, slot, std::vector<int>(m->n + 1)};
+  CU(cudaStreamSynchronize(m->st));
+  CU(cudaMemcpy(c.r.data(), m->dm.rank + (size_t)slot * (m->n + 1), (m->n + 1) * 4, cudaMemcpyDeviceToHost));
+  if (m->tc.err) CU(cudaMemsetAsync(m->tc.err, 0, sizeof(int), m->st));
   CU(cudaEventRecord(m->ev[2], m->st));
-  int launches = 0;
-  CU(launch_right_envs(m->dm, m->prec, slot, m->w, m->st));
-  ++launches;
-  // root environment L_0 = [1]
-  static const double one_d[2] = {1.0, 0.0};
-  static const float one_f[2] = {1.0f, 0.0f};
-  CU(cudaMemcpyAsync(m->w.L[0], m->prec == MPS_FP64 ? (const void*)one_d : (const void*)one_f, m->es,
-                     cudaMemcpyHostToDevice, m->st));
+  CU(launch_right_envs(m->dm, m->prec, slot, c.r.data(), m->w, m->st, &c.launches));
   const Trie& t = h->trie;
-  for (int k = 0; k < t.n_levels; ++k) {
-    TrieLevelDev lv{};
-    lv.n_nodes = t.level_nodes[k];
-    if (k + 1 < h->n && k + 1 < t.n_levels) {
-      lv.n_children = t.level_nodes[k + 1];
-      lv.parent = h->d_parent[k + 1];
-      lv.edge = h->d_edge[k + 1];
-    }
-    lv.n_closes = (int32_t)t.close_term[k].size();
-    lv.close_node = h->d_cnode[k];
-    lv.close_letter = h->d_cletter[k];
-    lv.close_term = h->d_cterm[k];
-    CU(launch_level(m->dm, m->prec, slot, m->w, k, lv, k & 1, m->st, &launches));
+  if (t.n_levels > 0) {
+    // root environment L_0 = [1] (one node, D_0 = 1)
+    static const double one_d[2] = {1.0, 0.0};
+    static const float one_f[2] = {1.0f, 0.0f};
+    CU(cudaMemcpyAsync(m->lvl_L[0], m->prec == MPS_FP64 ? (const void*)one_d : (const void*)one_f, m->es,
+                       cudaMemcpyHostToDevice, m->st));
+    TRY(meas_chunk(c, 0, 0, t.level_nodes[0]));
   }
   CU(launch_energy_sum(m->dm, m->prec, slot, m->w, T, h->d_coeff, h->id_term >= 0 ? h->id_coeff : 0.0,
                        h->id_term, m->st));
-  ++launches;
+  ++c.launches;
   CU(cudaEventRecord(m->ev[3], m->st));
   CU(cudaMemcpyAsync(out_host, m->w.out, (4 + (terms ? 2 * (size_t)T : 0)) * 8, cudaMemcpyDeviceToHost, m->st));
+  int tc_err = 0;
+  if (m->tc.err) CU(cudaMemcpyAsync(&tc_err, m->tc.err, sizeof(int), cudaMemcpyDeviceToHost, m->st));
   CU(cudaStreamSynchronize(m->st));
   float ms = 0;
   CU(cudaEventElapsedTime(&ms, m->ev[2], m->ev[3]));
   m->stats.ms_measure += ms;
-  m->stats.kernel_launches += launches;
+  m->stats.kernel_launches += c.launches;
+  if (tc_err) return fail(MPS_ETIMEOUT, "a bounded wait of the tensor-core GEMM pipeline ran out");
   return MPS_OK;
 }
 
@@ -546,7 +684,7 @@ int circ_destroy(circ_t c) {
 int mps_estimate_bytes(int n_qubits, int chi, int precision, int n_slots, circ_t circ, ham_t ham,
                        size_t* bytes) {
   if (!bytes) return fail(MPS_EINVAL, "mps_estimate_bytes: null pointer");
-  if (n_qubits < 2 || n_qubits > kMaxQubits || chi < 1 || chi > 128 || n_slots < 1 ||
+  if (n_qubits < 2 || n_qubits > kMaxQubits || chi < 1 || chi > kMaxChi || n_slots < 1 ||
       (precision != MPS_FP64 && precision != MPS_MIXED))
     return fail(MPS_EINVAL, "mps_estimate_bytes: bad sizes");
   const int n = n_qubits;
@@ -567,9 +705,10 @@ int mps_estimate_bytes(int n_qubits, int chi, int precision, int n_slots, circ_t
   if (circ) b += circ->comp.gates.size() * sizeof(GateRec) + circ->comp.mats.size() * 16 +
                  S * std::max(1, circ->comp.n_params) * 8;
   if (ham) {
-    const size_t T = ham->terms.size(), nodes = std::max<int32_t>(1, ham->trie.max_level_nodes);
-    b += 4 * nodes * chi2 * es + (4 + 4 * T) * 8;   // L (two levels), T, values
-    b += T * (8 + 4 + 1 + 4) + T * (size_t)n;       // coefficients and the trie arrays
+    const size_t T = ham->terms.size();
+    const MeasPlan plan = meas_plan(ham->trie, chi, es, precision == MPS_MIXED);
+    b += plan.level_bytes + plan.tc_bytes + (4 + 4 * T) * 8;   // chunk buffers, tensor-core scratch, values
+    b += T * (8 + 4 + 1 + 4) + T * (size_t)n;                  // coefficients and the trie arrays
   }
   *bytes = b;
   return MPS_OK;
@@ -578,7 +717,7 @@ int mps_estimate_bytes(int n_qubits, int chi, int precision, int n_slots, circ_t
 int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_stream, mps_t* out) {
   if (!out) return fail(MPS_EINVAL, "mps_create: null pointer");
   if (n_qubits < 2 || n_qubits > kMaxQubits) return fail(MPS_EINVAL, "mps_create: n_qubits out of [2, 128]");
-  if (chi < 1 || chi > 128) return fail(MPS_EINVAL, "mps_create: chi out of [1, 128]");
+  if (chi < 1 || chi > kMaxChi) return fail(MPS_EINVAL, "mps_create: chi out of [1, 256]");
   if (precision != MPS_FP64 && precision != MPS_MIXED) return fail(MPS_EINVAL, "mps_create: bad precision");
   if (n_slots < 1 || n_slots > 4096) return fail(MPS_EINVAL, "mps_create: n_slots out of [1, 4096]");
   reset_alloc_count();
@@ -609,27 +748,27 @@ int mps_create(int n_qubits, int chi, int precision, int n_slots, void* cuda_str
   d.slot_elems = off;
   const size_t mm = 2 * (size_t)chi;
   void* p;
-  TRY(dev_alloc(&p, (size_t)n_slots * off * m->es, "mps_create: B"));
+  TRY(dev_alloc(&p, (size_t)n_slots * off * m->es, "mps_create: B", m->st));
   d.B = p;
-  TRY(dalloc(&d.lam, (size_t)n_slots * (n - 1) * chi));
-  TRY(dalloc(&d.rank, (size_t)n_slots * (n + 1)));
-  TRY(dev_alloc(&p, (size_t)n_slots * mm * mm * m->es, "mps_create: work_M"));
+  TRY(dalloc(&d.lam, (size_t)n_slots * (n - 1) * chi, m->st));
+  TRY(dalloc(&d.rank, (size_t)n_slots * (n + 1), m->st));
+  TRY(dev_alloc(&p, (size_t)n_slots * mm * mm * m->es, "mps_create: work_M", m->st));
   d.work_M = p;
-  TRY(dev_alloc(&p, (size_t)n_slots * mm * (mm + 16) * m->es, "mps_create: work_X"));
+  TRY(dev_alloc(&p, (size_t)n_slots * mm * (mm + 16) * m->es, "mps_create: work_X", m->st));
   d.work_X = p;
-  TRY(dev_alloc(&p, (size_t)n_slots * 16 * chi * chi * sizeof(double), "mps_create: work_S"));
+  TRY(dev_alloc(&p, (size_t)n_slots * 16 * chi * chi * sizeof(double), "mps_create: work_S", m->st));
   d.work_S = p;
-  TRY(dalloc(&d.dw, n_slots));
-  TRY(dalloc(&d.stat, (size_t)n_slots * 4));
-  TRY(dalloc(&d.prof, (size_t)n_slots * 8));
-  CU(cudaMemset(d.prof, 0, (size_t)n_slots * 8 * 8));
-  TRY(dalloc(&m->d_site_off, n));
-  CU(cudaMemcpy(m->d_site_off, m->site_off.data(), n * 8, cudaMemcpyHostToDevice));
+  TRY(dalloc(&d.dw, n_slots, m->st));
+  TRY(dalloc(&d.stat, (size_t)n_slots * kStatWords, m->st));
+  TRY(dalloc(&d.prof, (size_t)n_slots * 8, m->st));
+  CU(cudaMemsetAsync(d.prof, 0, (size_t)n_slots * 8 * 8, m->st));
+  TRY(dalloc(&m->d_site_off, n, m->st));
+  CU(cudaMemcpyAsync(m->d_site_off, m->site_off.data(), n * 8, cudaMemcpyHostToDevice, m->st));
   d.site_off = m->d_site_off;
-  TRY(dalloc(&m->d_occ, (size_t)n_slots * n));
-  TRY(dalloc(&m->d_start_gate, n_slots));
-  TRY(dalloc(&m->d_shift_gate, n_slots));
-  TRY(dalloc(&m->d_shift_val, n_slots));
+  TRY(dalloc(&m->d_occ, (size_t)n_slots * n, m->st));
+  TRY(dalloc(&m->d_start_gate, n_slots, m->st));
+  TRY(dalloc(&m->d_shift_gate, n_slots, m->st));
+  TRY(dalloc(&m->d_shift_val, n_slots, m->st));
   for (auto& e : m->ev) CU(cudaEventCreate(&e));
   std::vector<uint8_t> zeros((size_t)n_slots * n, 0);
   TRY(upload_reset(m.get(), 0, n_slots, zeros.data()));
@@ -663,23 +802,52 @@ int mps_set_svd_params(mps_t m, double cutoff, int max_sweeps) {
   return MPS_OK;
 }
 
-static int finish_apply(mps_s* m, double* discarded_weight) {
-  double dw = 0;
-  int st4[4];
-  TRY(read_slot_stats(m, 0, &dw, st4));
+// Status of slots [slot0, slot0 + count) after a circuit launch. Slot slot0's figures
+// fill the per-call statistics; the counts of Jacobi caps and skipped non-finite gates
+// are summed over the slots. Returns MPS_ENONFINITE if any slot skipped a gate whose M'
+// held a NaN or Inf, else MPS_ENOCONV if any Jacobi fallback reached its sweep cap.
+int mps_set_meas_budget(mps_t m, size_t bytes) {
+  if (!m) return fail(MPS_EINVAL, "mps_set_meas_budget: null handle");
+  // a new budget takes effect at the next measurement; buffers are rebuilt to match
+  CU(cudaStreamSynchronize(m->st));
+  for (void*& p : m->lvl_L) {
+    dfree(p, m->st);
+    p = nullptr;
+  }
+  for (void*& p : m->lvl_T) {
+    dfree(p, m->st);
+    p = nullptr;
+  }
+  std::fill(m->lvl_cap.begin(), m->lvl_cap.end(), 0);
+  m->meas_budget = bytes;
+  return MPS_OK;
+}
+
+static int finish_apply(mps_s* m, double* discarded_weight, int slot0 = 0, int count = 1) {
+  std::vector<double> dws((size_t)count);
+  std::vector<int> st((size_t)count * kStatWords);
+  CU(cudaMemcpy(dws.data(), m->dm.dw + slot0, (size_t)count * 8, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(st.data(), m->dm.stat + (size_t)kStatWords * slot0, st.size() * 4, cudaMemcpyDeviceToHost));
   unsigned long long pr[8];
-  CU(cudaMemcpy(pr, m->dm.prof, sizeof(pr), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(pr, m->dm.prof + (size_t)slot0 * 8, sizeof(pr), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 7; ++i) m->stats.cycles[i] = (double)pr[i];
   double fl;
   std::memcpy(&fl, &pr[7], 8);
   m->stats.alg_flops_total = fl;
-  m->stats.discarded_weight = dw;
-  m->stats.max_sweeps = st4[0];
-  m->stats.n_svd_noconv = st4[1];
-  m->stats.max_rank = st4[2];
-  m->stats.n_fallback = st4[3];
-  if (discarded_weight) *discarded_weight = dw;
-  if (st4[1] > 0) return fail(MPS_ENOCONV, "a Jacobi SVD fallback reached its sweep cap");
+  m->stats.discarded_weight = dws[0];
+  m->stats.max_sweeps = st[0];
+  m->stats.max_rank = st[2];
+  m->stats.n_fallback = st[3];
+  int64_t noconv = 0, nonfinite = 0;
+  for (int s = 0; s < count; ++s) {
+    noconv += st[(size_t)s * kStatWords + 1];
+    nonfinite += st[(size_t)s * kStatWords + 4];
+  }
+  m->stats.n_svd_noconv += noconv;
+  m->stats.n_nonfinite += nonfinite;
+  if (discarded_weight) *discarded_weight = dws[0];
+  if (nonfinite > 0) return fail(MPS_ENONFINITE, "a gate's M' held a NaN or Inf; the gate was skipped");
+  if (noconv > 0) return fail(MPS_ENOCONV, "a Jacobi SVD fallback reached its sweep cap");
   return MPS_OK;
 }
 
@@ -690,7 +858,7 @@ int mps_apply_circuit(mps_t m, circ_t c, const double* theta, double* discarded_
   reset_stats(m);
   // the discarded-weight accumulator and stats of slot 0 restart at this call
   CU(cudaMemsetAsync(m->dm.dw, 0, 8, m->st));
-  CU(cudaMemsetAsync(m->dm.stat, 0, 16, m->st));
+  CU(cudaMemsetAsync(m->dm.stat, 0, 4 * kStatWords, m->st));
   TRY(run_circuit(m, c, 0, 1, theta));
   return finish_apply(m, discarded_weight);
 }
@@ -713,7 +881,7 @@ int mps_apply_gates(mps_t m, int64_t n_gates, const int32_t* bond, const double*
   }
   reset_stats(m);
   CU(cudaMemsetAsync(m->dm.dw, 0, 8, m->st));
-  CU(cudaMemsetAsync(m->dm.stat, 0, 16, m->st));
+  CU(cudaMemsetAsync(m->dm.stat, 0, 4 * kStatWords, m->st));
   TRY(run_circuit(m, &c, 0, 1, nullptr));
   return finish_apply(m, discarded_weight);
 }
@@ -843,6 +1011,16 @@ int mps_set_state(mps_t m, int slot, const int32_t* ranks, const double* B, cons
   return MPS_OK;
 }
 
+int mps_energy(mps_t m, ham_t h, double* energy) {
+  if (!m || !h || !energy) return fail(MPS_EINVAL, "mps_energy: null pointer");
+  if (h->n != m->n) return fail(MPS_EINVAL, "mps_energy: qubit count mismatch");
+  reset_stats(m);
+  m->h_out.resize(4 + 2 * h->terms.size());
+  TRY(run_measure(m, h, 0, m->h_out.data(), false));
+  *energy = m->h_out[0];
+  return MPS_OK;
+}
+
 int vqe_energy(mps_t m, circ_t c, ham_t h, const double* theta, double* energy) {
   return vqe_energy_batch(m, c, h, 1, theta, energy);
 }
@@ -857,7 +1035,7 @@ int vqe_energy_batch(mps_t m, circ_t c, ham_t h, int n_batch, const double* thet
   for (int b = 0; b < n_batch; ++b) std::memcpy(&occ[(size_t)b * m->n], c->comp.reference.data(), m->n);
   TRY(upload_reset(m, 0, n_batch, occ.data()));
   TRY(run_circuit(m, c, 0, n_batch, thetas));
-  int rc = finish_apply(m, nullptr);
+  int rc = finish_apply(m, nullptr, 0, n_batch);
   if (rc != MPS_OK && rc != MPS_ENOCONV) return rc;
   m->h_out.resize(4 + 2 * h->terms.size());
   for (int b = 0; b < n_batch; ++b) {
@@ -905,6 +1083,8 @@ int vqe_gradient(mps_t m, circ_t c, ham_t h, const double* theta, int n_sel, con
     if (rc == MPS_ENOCONV) rc_all = MPS_ENOCONV;
     return rc == MPS_OK || rc == MPS_ENOCONV;
   };
+  // a skipped non-finite gate ends the gradient with its own status
+  auto stop = [&](int rc) { return rc == MPS_ENONFINITE ? rc : MPS_ECUDA; };
   if (m->n_slots < 3) {
     // one slot: every shifted circuit from the reference state
     for (const Target& t : tg) {
@@ -914,7 +1094,10 @@ int vqe_gradient(mps_t m, circ_t c, ham_t h, const double* theta, int n_sel, con
         const double ph = sgn == 0 ? kHalfPi : -kHalfPi;
         TRY(upload_reset(m, 0, 1, ref.data()));
         TRY(run_circuit(m, c, 0, 1, theta, &zero, &sg, &ph));
-        if (!keep(finish_apply(m, nullptr))) return MPS_ECUDA;
+        {
+          const int rc = finish_apply(m, nullptr);
+          if (!keep(rc)) return stop(rc);
+        }
         TRY(run_measure(m, h, 0, m->h_out.data(), false));
         e2[sgn] = m->h_out[0];
       }
@@ -938,7 +1121,10 @@ int vqe_gradient(mps_t m, circ_t c, ham_t h, const double* theta, int n_sel, con
       if (t.gate > trunk) {
         const int64_t st0 = trunk;
         TRY(run_circuit(m, c, 0, 1, th.data(), &st0, nullptr, nullptr, t.gate));
-        if (!keep(finish_apply(m, nullptr))) return MPS_ECUDA;
+        {
+          const int rc = finish_apply(m, nullptr);
+          if (!keep(rc)) return stop(rc);
+        }
         trunk = t.gate;
       }
       for (int sgn = 0; sgn < 2; ++sgn) {
@@ -949,11 +1135,9 @@ int vqe_gradient(mps_t m, circ_t c, ham_t h, const double* theta, int n_sel, con
       }
     }
     TRY(run_circuit(m, c, 1, 2 * nw, th.data() + np, start.data(), sgate.data(), sphi.data(), G));
-    for (int s = 1; s <= 2 * nw; ++s) {
-      double dw;
-      int st4[4];
-      TRY(read_slot_stats(m, s, &dw, st4));
-      if (st4[1] > 0) rc_all = MPS_ENOCONV;
+    {
+      const int rc = finish_apply(m, nullptr, 1, 2 * nw);
+      if (!keep(rc)) return stop(rc);
     }
     for (int i = 0; i < nw; ++i) {
       double e2[2];

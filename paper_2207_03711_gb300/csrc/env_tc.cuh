@@ -1,0 +1,31 @@
+// Environment contractions of the trie measurement on the tensor cores (mixed
+// precision); see env_tc.cu for the GEMM formulation.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "cx.cuh"
+
+namespace mpsvqe {
+
+// Scratch of one handle for chunks of up to max_nodes trie nodes at bond cap chi.
+struct EnvTc {
+  float* scratch = nullptr;   // env_tc_scratch_floats(chi, max_nodes) floats, 256-byte aligned
+  int* err = nullptr;         // device int: set by a tensor-core pipeline wait that ran out
+  int chi = 0;
+  int max_nodes = 0;
+};
+
+size_t env_tc_scratch_floats(int chi, int max_nodes);
+
+// Shared operands of site k (D = left bond, Dp = right bond), once per level chunk.
+cudaError_t env_tc_site(const EnvTc& s, const Cx<float>* Bk, int D, int Dp, cudaStream_t st);
+// T_j[u] = L[u] B^j for U nodes (U <= max_nodes).
+cudaError_t env_tc_T(const EnvTc& s, const Cx<float>* L, Cx<float>* T, int U, int D, int Dp, cudaStream_t st);
+// L of the nc children whose parents are buffer entries [pa, pb) of T (trie index of
+// entry 0 is node_base), from C_ij = (B^i)^+ T_j and the edge letters.
+cudaError_t env_tc_children(const EnvTc& s, const Cx<float>* T, int pa, int pb, int D, int Dp,
+                            const int32_t* parent, const uint8_t* edge, int nc, int node_base, Cx<float>* Lout,
+                            cudaStream_t st);
+
+}  // namespace mpsvqe

@@ -46,7 +46,7 @@ __global__ void k_reset(DevMPS m, int slot0, const uint8_t* occ) {
   for (int b = threadIdx.x; b <= m.n; b += blockDim.x) rank[b] = 1;
   for (int b = threadIdx.x; b < m.n - 1; b += blockDim.x) lam[(size_t)b * m.chi] = 1.0;
   if (threadIdx.x == 0) m.dw[s] = 0.0;
-  if (threadIdx.x < 4) m.stat[s * 4 + threadIdx.x] = (threadIdx.x == 2) ? 1 : 0;  // passes, noconv, max rank, fallbacks
+  if (threadIdx.x < kStatWords) m.stat[s * kStatWords + threadIdx.x] = (threadIdx.x == 2) ? 1 : 0;
 }
 
 cudaError_t launch_reset(const DevMPS& m, int prec, int slot0, int count, const uint8_t* occ,
@@ -61,7 +61,8 @@ cudaError_t launch_reset(const DevMPS& m, int prec, int slot0, int count, const 
 // ------------------------------------------------------------ small tiled GEMM
 // C (Mdim x Ndim, ldc) = sum_t s_t opA_t(A_t) opB_t(B_t) with NTH threads (256 or 512)
 // and 64x64 tiles. opA: A stored Mdim x K (lda), or K x Mdim used as A^H (conjT).
-// opB: B stored K x Ndim (ldb), or Ndim x K used as B^T (transB).
+// opB: B stored K x Ndim (ldb), or Ndim x K used as B^T (transB); conjB conjugates the
+// entries of B as they are loaded.
 template <class R>
 struct GemmTerm {
   const Cx<R>* A;
@@ -71,61 +72,151 @@ struct GemmTerm {
   int ldb;
   Cx<R> s;
   bool transB;
+  bool conjB = false;
 };
 
+// One 64 x 64 output tile at (m0, n0).
 template <class R, int NTH>
-__device__ void block_gemm(int Mdim, int Ndim, int K, const GemmTerm<R>* terms, int nterm, Cx<R>* C,
-                           int ldc, Cx<R> (*As)[17], Cx<R> (*Bs)[65]) {
+__device__ void gemm_tile(int m0, int n0, int Mdim, int Ndim, int K, const GemmTerm<R>* terms, int nterm, Cx<R>* C,
+                          int ldc, Cx<R> (*As)[17], Cx<R> (*Bs)[65]) {
   constexpr int TY = NTH / 16, RPT = 64 / TY;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  for (int m0 = 0; m0 < Mdim; m0 += 64)
-    for (int n0 = 0; n0 < Ndim; n0 += 64) {
-      Cx<R> acc[RPT][4];
+  Cx<R> acc[RPT][4];
 #pragma unroll
-      for (int i = 0; i < RPT; ++i)
+  for (int i = 0; i < RPT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = cx<R>(0, 0);
-      for (int t = 0; t < nterm; ++t) {
-        const GemmTerm<R> T = terms[t];
-        for (int k0 = 0; k0 < K; k0 += 16) {
-          for (int e = threadIdx.x; e < 64 * 16; e += NTH) {
-            const int r = e >> 4, cc = e & 15;
-            const int gm = m0 + r, gk = k0 + cc;
-            Cx<R> v = cx<R>(0, 0);
-            if (gm < Mdim && gk < K) v = T.conjT ? conj(T.A[(size_t)gk * T.lda + gm]) : T.A[(size_t)gm * T.lda + gk];
-            As[r][cc] = T.s * v;
-          }
-          for (int e = threadIdx.x; e < 16 * 64; e += NTH) {
-            const int r = T.transB ? (e & 15) : (e >> 6), cc = T.transB ? (e >> 4) : (e & 63);
-            const int gk = k0 + r, gn = n0 + cc;
-            Cx<R> v = cx<R>(0, 0);
-            if (gk < K && gn < Ndim) v = T.transB ? T.B[(size_t)gn * T.ldb + gk] : T.B[(size_t)gk * T.ldb + gn];
-            Bs[r][cc] = v;
-          }
-          __syncthreads();
-#pragma unroll 4
-          for (int kk = 0; kk < 16; ++kk) {
-            Cx<R> a[RPT], b[4];
-#pragma unroll
-            for (int i = 0; i < RPT; ++i) a[i] = As[ty + TY * i][kk];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-            for (int i = 0; i < RPT; ++i)
-#pragma unroll
-              for (int j = 0; j < 4; ++j) cmac(acc[i][j], a[i], b[j]);
-          }
-          __syncthreads();
-        }
+    for (int j = 0; j < 4; ++j) acc[i][j] = cx<R>(0, 0);
+  for (int t = 0; t < nterm; ++t) {
+    const GemmTerm<R> T = terms[t];
+    for (int k0 = 0; k0 < K; k0 += 16) {
+      for (int e = threadIdx.x; e < 64 * 16; e += NTH) {
+        const int r = e >> 4, cc = e & 15;
+        const int gm = m0 + r, gk = k0 + cc;
+        Cx<R> v = cx<R>(0, 0);
+        if (gm < Mdim && gk < K) v = T.conjT ? conj(T.A[(size_t)gk * T.lda + gm]) : T.A[(size_t)gm * T.lda + gk];
+        As[r][cc] = T.s * v;
       }
+      for (int e = threadIdx.x; e < 16 * 64; e += NTH) {
+        const int r = T.transB ? (e & 15) : (e >> 6), cc = T.transB ? (e >> 4) : (e & 63);
+        const int gk = k0 + r, gn = n0 + cc;
+        Cx<R> v = cx<R>(0, 0);
+        if (gk < K && gn < Ndim) v = T.transB ? T.B[(size_t)gn * T.ldb + gk] : T.B[(size_t)gk * T.ldb + gn];
+        Bs[r][cc] = T.conjB ? conj(v) : v;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < 16; ++kk) {
+        Cx<R> a[RPT], b[4];
 #pragma unroll
-      for (int i = 0; i < RPT; ++i)
+        for (int i = 0; i < RPT; ++i) a[i] = As[ty + TY * i][kk];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int gm = m0 + ty + TY * i, gn = n0 + tx + 16 * j;
-          if (gm < Mdim && gn < Ndim) C[(size_t)gm * ldc + gn] = acc[i][j];
-        }
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cmac(acc[i][j], a[i], b[j]);
+      }
+      __syncthreads();
     }
+  }
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gm = m0 + ty + TY * i, gn = n0 + tx + 16 * j;
+      if (gm < Mdim && gn < Ndim) C[(size_t)gm * ldc + gn] = acc[i][j];
+    }
+}
+
+template <class R, int NTH>
+__device__ void block_gemm(int Mdim, int Ndim, int K, const GemmTerm<R>* terms, int nterm, Cx<R>* C, int ldc,
+                           Cx<R> (*As)[17], Cx<R> (*Bs)[65]) {
+  for (int m0 = 0; m0 < Mdim; m0 += 64)
+    for (int n0 = 0; n0 < Ndim; n0 += 64) gemm_tile<R, NTH>(m0, n0, Mdim, Ndim, K, terms, nterm, C, ldc, As, Bs);
+}
+
+// The same product spread over a grid: one 64 x 64 tile per thread block, blockIdx.z
+// selecting one of up to two independent products.
+template <class R>
+struct GridGemm {
+  GemmTerm<R> t[2][2];
+  int nterm;
+  Cx<R>* C[2];
+  int ldc, M, N, K;
+};
+
+template <class R>
+__global__ void __launch_bounds__(256) k_cgemm_grid(GridGemm<R> g) {
+  __shared__ Cx<R> As[64][17];
+  __shared__ Cx<R> Bs[16][65];
+  const int z = blockIdx.z;
+  gemm_tile<R, 256>(blockIdx.y * 64, blockIdx.x * 64, g.M, g.N, g.K, g.t[z], g.nterm, g.C[z], g.ldc, As, Bs);
+}
+
+// ------------------------------------------------ compensated re-orthonormalisation
+// Error-free transformations in FP32: TwoSum (Knuth) and the FMA form of TwoProd, the
+// building blocks of the compensated dot product "Dot2" (Ogita, Rump and Oishi, 2005),
+// which returns a dot product as accurate as if it were accumulated in twice the
+// working precision. The _rn intrinsics keep the compiler from contracting the
+// products into the sums, which would break the error-free transformations.
+__device__ __forceinline__ void dot2_acc(float a, float b, float& s, float& c) {
+  const float p = __fmul_rn(a, b);
+  const float ep = fmaf(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float bv = __fsub_rn(t, s);
+  const float et = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(ep, et));
+}
+
+// Rows x_0..x_{k-1} (length len, row stride ldx) of X are close to orthonormal; one
+// Newton-Schulz step X <- X - (1/2) E X with E = X X^H - I pulls them to
+// orthonormality up to the rounding of the update. E is tiny (a few 1e-7 after the
+// FP32 back-transformation), so it is only useful if the Gram matrix is accurate far
+// below FP32 resolution: each entry is a Dot2 sum. Xs (k x ldx) and Es (k x k) are
+// staging areas; the result is written to out (row stride len).
+template <int NT>
+__device__ void newton_schulz_rows(const Cx<float>* X, int k, int len, Cx<float>* Xs, int ldx, Cx<float>* Es,
+                                   Cx<float>* out) {
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < k * len; idx += NT) {
+    const int i = idx / len, q = idx - i * len;
+    Xs[(size_t)i * ldx + q] = X[idx];
+  }
+  __syncthreads();
+  const int npair = k * (k + 1) / 2;
+  for (int e = tid; e < npair; e += NT) {
+    // e -> (i, j), i <= j, rows of the upper triangle in order
+    int i = (int)((2.0f * k + 1.0f - sqrtf((2.0f * k + 1.0f) * (2.0f * k + 1.0f) - 8.0f * e)) * 0.5f);
+    while (i > 0 && i * k - i * (i - 1) / 2 > e) --i;
+    while ((i + 1) * k - (i + 1) * i / 2 <= e) ++i;
+    const int j = i + (e - (i * k - i * (i - 1) / 2));
+    const Cx<float>* xi = Xs + (size_t)i * ldx;
+    const Cx<float>* xj = Xs + (size_t)j * ldx;
+    float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+    for (int q = 0; q < len; ++q) {
+      const Cx<float> a = xi[q], b = xj[q];
+      // G_ij = sum_q a conj(b)
+      dot2_acc(a.x, b.x, sr, cr);
+      dot2_acc(a.y, b.y, sr, cr);
+      dot2_acc(a.y, b.x, si, ci);
+      dot2_acc(-a.x, b.y, si, ci);
+    }
+    // the diagonal is within 1e-6 of 1, so sr - 1 is exact (Sterbenz)
+    const float er = __fadd_rn(i == j ? __fsub_rn(sr, 1.0f) : sr, cr);
+    const float ei = i == j ? 0.0f : __fadd_rn(si, ci);
+    Es[(size_t)i * k + j] = cx<float>(er, ei);
+    Es[(size_t)j * k + i] = cx<float>(er, -ei);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < k * len; idx += NT) {
+    const int i = idx / len, q = idx - i * len;
+    Cx<float> acc = cx<float>(0.f, 0.f);
+    for (int j = 0; j < k; ++j) cmac(acc, Es[(size_t)i * k + j], Xs[(size_t)j * ldx + q]);
+    const Cx<float> x = Xs[(size_t)i * ldx + q];
+    out[idx] = cx<float>(x.x - 0.5f * acc.x, x.y - 0.5f * acc.y);
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------- gate engine
@@ -152,6 +243,14 @@ __device__ __forceinline__ double flops_per_gate(int rl, int rm, int rr, int k) 
   const double svd = 4.0 * (4.0 * big * small * small + 8.0 * small * small * small);
   const double update = 8.0 * m * n * k;
   return contract + svd + update;
+}
+
+// Capacity of bond b (b = -1 and b = n-1 are the trivial outer bonds): the largest rank
+// an n-site MPS with bond cap chi can have there, min(chi, 2^min(b+1, n-1-b)).
+__device__ __forceinline__ int bond_cap(int b, int n, int chi) {
+  if (b < 0 || b >= n - 1) return 1;
+  const int e = min(min(b + 1, n - 1 - b), 30);
+  return min(chi, 1 << e);
 }
 
 template <class R>
@@ -229,7 +328,7 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
   Cx<R>* T = TS ? (Cx<R>*)(smem + L.t_off) : (Cx<R>*)m.work_X + (size_t)s * mmax * (mmax + 16);
   const double* th = theta + (size_t)blockIdx.x * c.n_params;
 
-  int st_max_iters = 0, st_max_rank = 1, st_bad = 0;
+  int st_max_iters = 0, st_max_rank = 1, st_bad = 0, st_nonfinite = 0, st_badarg = 0;
   if (threadIdx.x == 0) misc[2] = 0;
   {
     // per-launch tables: grid shifts over [10^-decades, 1] and, for kk targets, the
@@ -292,6 +391,20 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
       Uf[threadIdx.x] = cx<R>((R)u.x, (R)u.y);
     }
     const int bond = gr.bond;
+    if constexpr (RAW) {
+      // caller-owned device arrays: the bond and the three ranks it touches must lie
+      // inside the site capacities before anything is indexed (uniform over the block)
+      bool ok = bond >= 0 && bond <= n - 2;
+      if (ok) {
+        const int r0 = rank[bond], r1 = rank[bond + 1], r2 = rank[bond + 2];
+        ok = r0 >= 1 && r0 <= bond_cap(bond - 1, n, chi) && r1 >= 1 && r1 <= bond_cap(bond, n, chi) && r2 >= 1 &&
+             r2 <= bond_cap(bond + 1, n, chi);
+      }
+      if (!ok) {
+        if (threadIdx.x == 0) st_badarg = 1;
+        break;
+      }
+    }
     const int rl = rank[bond], rm = rank[bond + 1], rr = rank[bond + 2];
     const int mrows = 2 * rl, ncol = 2 * rr;
     const bool tall = mrows >= ncol;
@@ -346,6 +459,12 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     }
 
     __syncthreads();
+    // a NaN or Inf in M' (from corrupted inputs) would run through every later stage:
+    // the gate is skipped, the state left as it was, and the host reports the count
+    if (!(red[NT / 32] <= DBL_MAX)) {
+      if (threadIdx.x == 0) ++st_nonfinite;
+      continue;
+    }
     PHASE(0);
     // (3) Eq. (9): bidiagonalise T = Q B P^H (B real); the reflector vectors are staged
     //     in the (not yet used) singular-vector buffer
@@ -542,6 +661,15 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
       }
       __syncthreads();
     }
+    if constexpr (sizeof(R) == 4) {
+      // (5b) mixed precision: the FP32 back-transformation leaves the rows of V
+      //      orthonormal only to a few 1e-7; over a long circuit that defect, not the
+      //      rounding of the stored tensors, dominates the energy error. One compensated
+      //      Newton-Schulz step brings it down to the storage rounding. T is dead here
+      //      and stages V and E = V V^H - I.
+      const int ldx = ncol + 1;
+      newton_schulz_rows<NT>(xout, kf, ncol, T, ldx, T + (size_t)kf * ldx, xout);
+    }
     PHASE(5);
     // (6) Eq. (10): B_{n+1} <- V (row t = v_t^H), B_n <- M V^H (column t = M v_t),
     //     lambda_n <- sigma
@@ -561,11 +689,13 @@ __global__ void __launch_bounds__(NT) k_circuit(DevMPS m, CircDev c, int64_t g0,
     for (int i = 0; i < 7; ++i) m.prof[s * 8 + i] += ph[i];
     m.prof[s * 8 + 7] = __double_as_longlong(__longlong_as_double(m.prof[s * 8 + 7]) + alg_flops);
     m.dw[s] += dw_acc;
-    int* stt = m.stat + s * 4;
+    int* stt = m.stat + s * kStatWords;
     stt[0] = max(stt[0], st_max_iters);
     stt[1] += misc[2];
     stt[3] += st_bad;
     stt[2] = max(stt[2], st_max_rank);
+    stt[4] += st_nonfinite;
+    stt[5] |= st_badarg;
   }
 }
 
@@ -615,49 +745,54 @@ cudaError_t launch_circuit(const DevMPS& m, int prec, const CircDev& c, int64_t 
 }
 
 // --------------------------------------------------------- right environments
-// R_n = [1]; R_k = sum_i B_k^i R_{k+1} B_k^{i+}; Bhat_k^i = B_k^i R_{k+1} (same layout as B_k).
+// R_n = [1]; R_k = sum_i Bhat_k^i (B_k^i)^+ with Bhat_k^i = B_k^i R_{k+1} (same layout as
+// B_k). Per site two grid launches (the two Bhat^i products side by side, then R_k), so
+// large bond dimensions use many SMs. ranks: the slot's bond ranks on the host
+// (ranks[k] = left dimension of site k).
 template <class R>
-__global__ void __launch_bounds__(256) k_right_envs(DevMPS m, int slot, Cx<R>* Renv, Cx<R>* Bhat) {
-  __shared__ Cx<R> As[64][17];
-  __shared__ Cx<R> Bs[16][65];
-  const int n = m.n, chi2 = m.chi * m.chi;
+static cudaError_t right_envs_t(const DevMPS& m, int slot, const int* ranks, Cx<R>* Renv, Cx<R>* Bhat,
+                                cudaStream_t st) {
+  const int n = m.n;
+  const size_t chi2 = (size_t)m.chi * m.chi;
   const Cx<R>* Bslot = (const Cx<R>*)m.B + (size_t)slot * m.slot_elems;
-  const int* rank = m.rank + (size_t)slot * (n + 1);
-  if (threadIdx.x == 0) Renv[(size_t)n * chi2] = cx<R>(1, 0);
-  __syncthreads();
+  static const Cx<R> one = cx<R>(1, 0);
+  cudaError_t e = cudaMemcpyAsync(Renv + (size_t)n * chi2, &one, sizeof(Cx<R>), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
   for (int k = n - 1; k >= 0; --k) {
-    const int Dl = rank[k], Dr = rank[k + 1];
+    const int Dl = ranks[k], Dr = ranks[k + 1];
     const Cx<R>* Bk = Bslot + m.site_off[k];
     Cx<R>* Bh = Bhat + m.site_off[k];
     const Cx<R>* Rn = Renv + (size_t)(k + 1) * chi2;
-    for (int i = 0; i < 2; ++i) {  // Bhat^i = B^i R_{k+1}: (Dl x Dr)(Dr x Dr)
-      GemmTerm<R> t{Bk + i * Dr, 2 * Dr, false, Rn, Dr, cx<R>(1, 0), false};
-      block_gemm<R, 256>(Dl, Dr, Dr, &t, 1, Bh + i * Dr, 2 * Dr, As, Bs);
-      __syncthreads();
+    GridGemm<R> g{};
+    g.nterm = 1;
+    g.ldc = 2 * Dr;
+    g.M = Dl;
+    g.N = Dr;
+    g.K = Dr;
+    for (int i = 0; i < 2; ++i) {   // Bhat^i = B^i R_{k+1}: (Dl x Dr)(Dr x Dr)
+      g.t[i][0] = GemmTerm<R>{Bk + i * Dr, 2 * Dr, false, Rn, Dr, cx<R>(1, 0), false};
+      g.C[i] = Bh + i * Dr;
     }
-    // R_k = sum_i Bhat^i (B^i)^+ : (Dl x Dr)(Dr x Dl). As a product with A = Bhat^i and
-    // B = (B^i)^+ we use C^T-free form: R_k[a][a'] = sum_b Bhat[a][b] conj(B[a'][b]).
-    Cx<R>* Rk = Renv + (size_t)k * chi2;
-    for (int e = threadIdx.x; e < Dl * Dl; e += 256) {
-      const int a = e / Dl, ap = e - a * Dl;
-      Cx<R> acc = cx<R>(0, 0);
-      for (int i = 0; i < 2; ++i) {
-        const Cx<R>* hr = Bh + (size_t)(2 * a + i) * Dr;
-        const Cx<R>* br = Bk + (size_t)(2 * ap + i) * Dr;
-        for (int b = 0; b < Dr; ++b) cmac(acc, hr[b], conj(br[b]));
-      }
-      Rk[e] = acc;
-    }
-    __syncthreads();
+    k_cgemm_grid<R><<<dim3((Dr + 63) / 64, (Dl + 63) / 64, 2), 256, 0, st>>>(g);
+    // R_k = sum_i Bhat^i (B^i)^+: B^i read as (Dl x Dr) transposed and conjugated
+    GridGemm<R> h{};
+    h.nterm = 2;
+    h.ldc = Dl;
+    h.M = Dl;
+    h.N = Dl;
+    h.K = Dr;
+    for (int i = 0; i < 2; ++i) h.t[0][i] = GemmTerm<R>{Bh + i * Dr, 2 * Dr, false, Bk + i * Dr, 2 * Dr, cx<R>(1, 0), true, true};
+    h.C[0] = Renv + (size_t)k * chi2;
+    k_cgemm_grid<R><<<dim3((Dl + 63) / 64, (Dl + 63) / 64, 1), 256, 0, st>>>(h);
   }
+  return cudaGetLastError();
 }
 
-cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, MeasDev& w, cudaStream_t st) {
-  if (prec == MPS_PREC_FP64)
-    k_right_envs<double><<<1, 256, 0, st>>>(m, slot, (Cx<double>*)w.R, (Cx<double>*)w.Bhat);
-  else
-    k_right_envs<float><<<1, 256, 0, st>>>(m, slot, (Cx<float>*)w.R, (Cx<float>*)w.Bhat);
-  return cudaGetLastError();
+cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, const int* ranks, MeasDev& w, cudaStream_t st,
+                              int* launches) {
+  *launches += 2 * m.n;
+  if (prec == MPS_PREC_FP64) return right_envs_t<double>(m, slot, ranks, (Cx<double>*)w.R, (Cx<double>*)w.Bhat, st);
+  return right_envs_t<float>(m, slot, ranks, (Cx<float>*)w.R, (Cx<float>*)w.Bhat, st);
 }
 
 // ------------------------------------------------------------------ trie level
@@ -689,7 +824,8 @@ __global__ void __launch_bounds__(256) k_level_T(DevMPS m, int slot, int k, cons
 // L_{k+1}[c] = sum_ij sigma_ij (B_k^i)^+ T_j[parent(c)]
 template <class R>
 __global__ void __launch_bounds__(256) k_level_child(DevMPS m, int slot, int k, const int32_t* parent,
-                                                     const uint8_t* edge, const Cx<R>* T, Cx<R>* Lout) {
+                                                     const uint8_t* edge, const Cx<R>* T, Cx<R>* Lout,
+                                                     int node_base) {
   __shared__ Cx<R> As[64][17];
   __shared__ Cx<R> Bs[16][65];
   const int c = blockIdx.x;
@@ -697,7 +833,7 @@ __global__ void __launch_bounds__(256) k_level_child(DevMPS m, int slot, int k, 
   const int* rank = m.rank + (size_t)slot * (m.n + 1);
   const int Dk = rank[k], Dk1 = rank[k + 1];
   const Cx<R>* Bk = (const Cx<R>*)m.B + (size_t)slot * m.slot_elems + m.site_off[k];
-  const int u = parent[c];
+  const int u = parent[c] - node_base;
   int ii[2], jj[2];
   Cx<R> sg[2];
   letter_entries<R>(edge[c], ii, jj, sg);
@@ -711,14 +847,15 @@ __global__ void __launch_bounds__(256) k_level_child(DevMPS m, int slot, int k, 
 template <class R>
 __global__ void __launch_bounds__(256) k_level_close(DevMPS m, int slot, int k, const int32_t* cnode,
                                                      const uint8_t* cletter, const int32_t* cterm,
-                                                     const Cx<R>* T, const Cx<R>* Bhat, double* vals) {
+                                                     const Cx<R>* T, const Cx<R>* Bhat, double* vals,
+                                                     int node_base) {
   __shared__ double red[2][8];
   const int c = blockIdx.x;
   const int chi2 = m.chi * m.chi;
   const int* rank = m.rank + (size_t)slot * (m.n + 1);
   const int Dk = rank[k], Dk1 = rank[k + 1];
   const Cx<R>* Bh = Bhat + m.site_off[k];
-  const int u = cnode[c];
+  const int u = cnode[c] - node_base;
   int ii[2], jj[2];
   Cx<R> sg[2];
   letter_entries<R>(cletter[c], ii, jj, sg);
@@ -757,32 +894,39 @@ __global__ void __launch_bounds__(256) k_level_close(DevMPS m, int slot, int k, 
   }
 }
 
-template <class R>
-static cudaError_t launch_level_t(const DevMPS& m, int slot, MeasDev& w, int k, const TrieLevelDev& lv,
-                                  int parity, cudaStream_t st, int* launches) {
-  const Cx<R>* Lin = (const Cx<R>*)w.L[parity];
-  Cx<R>* Lout = (Cx<R>*)w.L[parity ^ 1];
-  Cx<R>* T = (Cx<R>*)w.T;
-  if (lv.n_nodes > 0) {
-    k_level_T<R><<<dim3(lv.n_nodes, 2), 256, 0, st>>>(m, slot, k, Lin, T);
-    ++*launches;
-  }
-  if (lv.n_closes > 0) {
-    k_level_close<R><<<lv.n_closes, 256, 0, st>>>(m, slot, k, lv.close_node, lv.close_letter, lv.close_term,
-                                                   T, (const Cx<R>*)w.Bhat, w.vals);
-    ++*launches;
-  }
-  if (lv.n_children > 0) {
-    k_level_child<R><<<lv.n_children, 256, 0, st>>>(m, slot, k, lv.parent, lv.edge, T, Lout);
-    ++*launches;
-  }
+cudaError_t launch_env_T(const DevMPS& m, int prec, int slot, int k, const void* L, void* T, int n_nodes,
+                         cudaStream_t st) {
+  if (n_nodes <= 0) return cudaSuccess;
+  if (prec == MPS_PREC_FP64)
+    k_level_T<double><<<dim3(n_nodes, 2), 256, 0, st>>>(m, slot, k, (const Cx<double>*)L, (Cx<double>*)T);
+  else
+    k_level_T<float><<<dim3(n_nodes, 2), 256, 0, st>>>(m, slot, k, (const Cx<float>*)L, (Cx<float>*)T);
   return cudaGetLastError();
 }
 
-cudaError_t launch_level(const DevMPS& m, int prec, int slot, MeasDev& w, int k, const TrieLevelDev& lv,
-                         int parity, cudaStream_t st, int* launches) {
-  if (prec == MPS_PREC_FP64) return launch_level_t<double>(m, slot, w, k, lv, parity, st, launches);
-  return launch_level_t<float>(m, slot, w, k, lv, parity, st, launches);
+cudaError_t launch_env_close(const DevMPS& m, int prec, int slot, int k, const void* T, const void* Bhat,
+                             const int32_t* cnode, const uint8_t* cletter, const int32_t* cterm, int n_closes,
+                             int node_base, double* vals, cudaStream_t st) {
+  if (n_closes <= 0) return cudaSuccess;
+  if (prec == MPS_PREC_FP64)
+    k_level_close<double><<<n_closes, 256, 0, st>>>(m, slot, k, cnode, cletter, cterm, (const Cx<double>*)T,
+                                                     (const Cx<double>*)Bhat, vals, node_base);
+  else
+    k_level_close<float><<<n_closes, 256, 0, st>>>(m, slot, k, cnode, cletter, cterm, (const Cx<float>*)T,
+                                                    (const Cx<float>*)Bhat, vals, node_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_env_child(const DevMPS& m, int prec, int slot, int k, const void* T, const int32_t* parent,
+                             const uint8_t* edge, int n_children, int node_base, void* Lout, cudaStream_t st) {
+  if (n_children <= 0) return cudaSuccess;
+  if (prec == MPS_PREC_FP64)
+    k_level_child<double><<<n_children, 256, 0, st>>>(m, slot, k, parent, edge, (const Cx<double>*)T,
+                                                       (Cx<double>*)Lout, node_base);
+  else
+    k_level_child<float><<<n_children, 256, 0, st>>>(m, slot, k, parent, edge, (const Cx<float>*)T,
+                                                      (Cx<float>*)Lout, node_base);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ energy sum
@@ -862,6 +1006,7 @@ constexpr int kNoAllocMaxChi = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[mpsvqe::kNoAllocScratchBytes];
 
+#include <cstring>
 #include <mutex>
 #include "../../include/mpsvqe.h"
 
@@ -948,8 +1093,27 @@ extern "C" int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors
     if (cudaGetLastError() != cudaSuccess) return MPS_ECUDA;
   }
   if (discarded_weight) {
-    if (cudaMemcpyAsync(discarded_weight, d.dw, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return MPS_ECUDA;
+    // the discarded weight and the status words sit next to each other in the array:
+    // one copy brings both back
+    unsigned char host[8 + 4 * kStatWords];
+    if (cudaMemcpyAsync(host, d.dw, sizeof(host), cudaMemcpyDeviceToHost, st) != cudaSuccess) return MPS_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return MPS_ECUDA;
+    int stat[kStatWords];
+    std::memcpy(discarded_weight, host, 8);
+    std::memcpy(stat, host + 8, sizeof(stat));
+    if (stat[5]) {
+      set_error_message("mps_apply_gates_noalloc: a bond outside [0, n-2] or a rank outside its capacity "
+                        "reached the device; gates from there on were not applied");
+      return MPS_EINVAL;
+    }
+    if (stat[4] > 0) {
+      set_error_message("mps_apply_gates_noalloc: a gate's M' held a NaN or Inf; the gate was skipped");
+      return MPS_ENONFINITE;
+    }
+    if (stat[1] > 0) {
+      set_error_message("mps_apply_gates_noalloc: a Jacobi SVD fallback reached its sweep cap");
+      return MPS_ENOCONV;
+    }
   }
   return MPS_OK;
 }

@@ -9,6 +9,13 @@ namespace mpsvqe {
 
 enum { MPS_PREC_FP64 = 0, MPS_PREC_MIXED = 1 };
 
+// Per-slot status words written by the gate engine: [0] most bisection passes of one
+// gate, [1] Jacobi fallbacks that hit their sweep cap, [2] largest rank reached,
+// [3] Jacobi fallbacks taken, [4] gates skipped because M' held a NaN or Inf,
+// [5] set when a caller-owned bond or rank array was out of range (raw-gate launches),
+// [6..7] unused.
+constexpr int kStatWords = 8;
+
 // Device view of n_slots MPS states that share one layout.
 struct DevMPS {
   int n;                    // sites
@@ -23,7 +30,7 @@ struct DevMPS {
   void* work_X;             // complex<R> [n_slots][2chi (2chi+16)]  M' when not in smem
   void* work_S;             // double [n_slots][16 chi^2]  SVD scratch (vectors, factorisations)
   double* dw;               // [n_slots] accumulated discarded weight
-  int* stat;                // [n_slots][4]: bisection passes, collapsed vectors, max rank, error flag
+  int* stat;                // [n_slots][kStatWords] status words (see kStatWords)
   unsigned long long* prof; // [n_slots][8] clock cycles per gate-engine phase (thread 0)
 };
 
@@ -54,29 +61,28 @@ cudaError_t launch_circuit(const DevMPS& m, int prec, const CircDev& c, int64_t 
 struct MeasDev {
   void* R;          // complex<R> [n+1][chi*chi] right identity environments R_k
   void* Bhat;       // complex<R> like one slot of B: B_k^i R_{k+1}
-  void* L[2];       // complex<R> [max_level_nodes][chi*chi] ping-pong left environments
-  void* T;          // complex<R> [max_level_nodes][2][chi*chi]
   double* vals;     // [n_terms][2] re, im of unnormalised <P>
   double* out;      // [4 + n_terms*2]: E, norm, ...
 };
 
-struct TrieLevelDev {
-  int32_t n_nodes;
-  int32_t n_children;          // nodes at level k+1
-  const int32_t* parent;       // [n_children] parent node at level k
-  const uint8_t* edge;         // [n_children]
-  int32_t n_closes;
-  const int32_t* close_node;
-  const uint8_t* close_letter;
-  const int32_t* close_term;
-};
 
 // Thread-local message returned by mps_last_error() (defined with the C ABI).
 void set_error_message(const char* msg);
 
-cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, MeasDev& w, cudaStream_t st);
-cudaError_t launch_level(const DevMPS& m, int prec, int slot, MeasDev& w, int k,
-                         const TrieLevelDev& lv, int parity, cudaStream_t st, int* launches);
+// ranks: the slot's n+1 bond ranks on the host (ranks[k] = left dimension of site k).
+cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, const int* ranks, MeasDev& w, cudaStream_t st,
+                              int* launches);
+// Chunked trie levels. Environment buffers: L holds node u's D_k x D_k block (row-major,
+// leading dimension D_k) at u chi^2 complex entries; T holds T_j[u] = L[u] B_k^j
+// (D_k x D_{k+1}, leading dimension D_{k+1}) at (2u + j) chi^2. Node indices in cnode /
+// parent are absolute trie indices; node_base is the trie index of buffer entry 0.
+cudaError_t launch_env_T(const DevMPS& m, int prec, int slot, int k, const void* L, void* T, int n_nodes,
+                         cudaStream_t st);
+cudaError_t launch_env_close(const DevMPS& m, int prec, int slot, int k, const void* T, const void* Bhat,
+                             const int32_t* cnode, const uint8_t* cletter, const int32_t* cterm, int n_closes,
+                             int node_base, double* vals, cudaStream_t st);
+cudaError_t launch_env_child(const DevMPS& m, int prec, int slot, int k, const void* T, const int32_t* parent,
+                             const uint8_t* edge, int n_children, int node_base, void* Lout, cudaStream_t st);
 // E = sum_t coeff_t Re(vals_t) / norm + id_coeff (Neumaier, fixed order); also writes
 // normalised <P_t> to out[4 + 2t], out[0] = E, out[1] = norm.
 cudaError_t launch_energy_sum(const DevMPS& m, int prec, int slot, MeasDev& w, int64_t n_terms,

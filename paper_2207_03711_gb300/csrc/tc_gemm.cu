@@ -1,0 +1,370 @@
+// Real GEMM on the fifth-generation tensor cores of sm_103a (tcgen05 + TMEM + TMA)
+// with compensated TF32 splits, the contraction primitive of the environment sweeps.
+//
+// C (M x N, FP32) = A (M x K) . B (N x K)^T, both operands K-major (row-major with K
+// contiguous). Each operand is given as two FP32 planes, hi = tf32(x) and
+// lo = tf32(x - hi); the product is accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi
+// in FP32 inside TMEM, which recovers the bits a single TF32 product drops (relative
+// error ~2^-21 instead of ~2^-11), i.e. an FP32-quality GEMM at tensor-core rate.
+//
+// One CTA computes one 128 x 256 tile of C with 192 threads:
+//   warp 0, lane 0  TMA producer: four K-major 128-byte-swizzled tiles per stage
+//                   (A_hi, A_lo: 128 x 32; B_hi, B_lo: 256 x 32), two stages
+//   warp 1          allocates 256 TMEM columns; lane 0 issues tcgen05.mma
+//                   (M 128, N 256, K 8) three times per K step and commits each
+//                   stage back to the producer through an mbarrier
+//   warps 2..5      epilogue: tcgen05.ld of the accumulator (warp w reads TMEM lanes
+//                   32 (w mod 4) ..), bounds-checked stores of C
+// Every mbarrier wait is bounded: a wait that runs out records an error code in
+// *err, and the kernel still passes its final barrier, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "tc_gemm.cuh"
+
+namespace mpsvqe {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 32;            // BK fp32 = 128 bytes = one swizzle row
+constexpr int STAGES = 2;
+constexpr int TILE_A = BM * BK * 4;                   // 16 KB
+constexpr int TILE_B = BN * BK * 4;                   // 32 KB
+constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // hi and lo of both operands: 96 KB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 128;
+constexpr int NTHREADS = 192;
+constexpr int TMEM_COLS = 256;
+constexpr long long kWaitCycles = 4000000000LL;       // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on the phase with the given parity; false (and *err set) on time-out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile stored as rows of 128 bytes with the
+// 128-byte swizzle (the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B): 8-row core
+// groups 1024 bytes apart (stride byte offset); the leading byte offset is not used by
+// this layout; version 1 (tcgen05); layout type 2 = SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: FP32 accumulator (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n"
+      " .reg .pred p;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, float* C,
+                  int64_t ldc, int M, int N, int K, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(base + STAGES * STAGE_BYTES);  // full[STAGES], empty[STAGES], done
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nk = (K + BK - 1) / BK;
+
+  if (tid == 0) {
+    for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmAh)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBh)) : "memory");
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES;
+      if (kt >= STAGES && !mbar_wait(smem_u32(&bars[STAGES + s]), ((kt / STAGES) & 1) ^ 1, err, 1)) break;
+      unsigned char* st = base + s * STAGE_BYTES;
+      const uint32_t full = smem_u32(&bars[s]);
+      mbar_arrive_expect_tx(full, STAGE_BYTES);
+      tma_load_2d(smem_u32(st), &tmAh, kt * BK, m0, full);
+      tma_load_2d(smem_u32(st + TILE_A), &tmAl, kt * BK, m0, full);
+      tma_load_2d(smem_u32(st + 2 * TILE_A), &tmBh, kt * BK, n0, full);
+      tma_load_2d(smem_u32(st + 2 * TILE_A + TILE_B), &tmBl, kt * BK, n0, full);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = idesc_tf32(BM, BN);
+    bool ok = true;
+    for (int kt = 0; kt < nk && ok; ++kt) {
+      const int s = kt % STAGES;
+      ok = mbar_wait(smem_u32(&bars[s]), (kt / STAGES) & 1, err, 2);
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = smem_u32(base + s * STAGE_BYTES);
+#pragma unroll
+      for (int ks = 0; ks < BK / 8; ++ks) {
+        // K step of 8 TF32 = 32 bytes inside each 128-byte swizzled row
+        const uint64_t ah = sw128_kmajor_desc(st + ks * 32);
+        const uint64_t al = sw128_kmajor_desc(st + TILE_A + ks * 32);
+        const uint64_t bh = sw128_kmajor_desc(st + 2 * TILE_A + ks * 32);
+        const uint64_t bl = sw128_kmajor_desc(st + 2 * TILE_A + TILE_B + ks * 32);
+        mma_tf32(tmem, ah, bh, idesc, (kt > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, ah, bl, idesc, 1u);
+        mma_tf32(tmem, al, bh, idesc, 1u);
+      }
+      mma_commit(smem_u32(&bars[STAGES + s]));   // stage s free once these finish
+    }
+    mma_commit(smem_u32(&bars[2 * STAGES]));     // accumulator complete
+  } else if (warp >= 2) {
+    // ---- epilogue
+    const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0, err, 3);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+      const int q = warp & 3;
+      const int row = m0 + q * 32 + lane;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+        if (row < M) {
+          float* out = C + (size_t)row * ldc + n0 + c0;
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (n0 + c0 + j < N) out[j] = v[j];
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// hi = tf32(x) (round to nearest, low 13 mantissa bits zero) and lo = tf32(x - hi) of an
+// M x K row-major plane (leading dimension ld_in) into two planes of leading dimension
+// ld_out (a multiple of 4 floats, so TMA rows start on 16-byte boundaries); columns
+// K..ld_out-1 are written as zero.
+__global__ void k_split_tf32(const float* x, int64_t ld_in, int M, int K, float* hi, float* lo, int64_t ld_out) {
+  const int64_t total = (int64_t)M * ld_out;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / ld_out, c = i - r * ld_out;
+    float h = 0.f, l = 0.f;
+    if (c < K) {
+      const float v = x[r * ld_in + c];
+      uint32_t hb, lb;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+      h = __uint_as_float(hb);
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(v - h));
+      l = __uint_as_float(lb);
+    }
+    hi[i] = h;
+    lo[i] = l;
+  }
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+cudaError_t g_encode_status = cudaSuccess;
+}  // namespace
+
+static cudaError_t get_encoder() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    g_encode_status = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (g_encode_status == cudaSuccess && (q != cudaDriverEntryPointSuccess || !fn))
+      g_encode_status = cudaErrorNotSupported;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  });
+  return g_encode_status;
+}
+
+// 2-D FP32 tensor map of a rows x K plane with leading dimension ld (floats): boxes of
+// 32 x box_rows, 128-byte swizzle, out-of-range elements read as zero.
+static cudaError_t make_map(CUtensorMap* map, const float* p, int rows, int K, int64_t ld, int box_rows) {
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(p), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_split_tf32(const float* x, int64_t ld_in, int M, int K, float* hi, float* lo, int64_t ld_out,
+                              cudaStream_t st) {
+  if (M <= 0 || ld_out <= 0) return cudaSuccess;
+  const int64_t total = (int64_t)M * ld_out;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+  k_split_tf32<<<blocks, 256, 0, st>>>(x, ld_in, M, K, hi, lo, ld_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tf32x3(const SplitPlane& A, const SplitPlane& B, int M, int N, int K, float* C, int64_t ldc,
+                               int* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if ((A.ld & 3) || (B.ld & 3) || ((uintptr_t)A.hi & 15) || ((uintptr_t)A.lo & 15) || ((uintptr_t)B.hi & 15) ||
+      ((uintptr_t)B.lo & 15))
+    return cudaErrorInvalidValue;
+  CUtensorMap ah, al, bh, bl;
+  cudaError_t e;
+  if ((e = make_map(&ah, A.hi, M, K, A.ld, BM)) != cudaSuccess) return e;
+  if ((e = make_map(&al, A.lo, M, K, A.ld, BM)) != cudaSuccess) return e;
+  if ((e = make_map(&bh, B.hi, N, K, B.ld, BN)) != cudaSuccess) return e;
+  if ((e = make_map(&bl, B.lo, N, K, B.ld, BN)) != cudaSuccess) return e;
+  static std::once_flag once[64];
+  static cudaError_t attr[64];
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::call_once(once[dev], [dev] {
+    attr[dev] = cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  });
+  if (attr[dev] != cudaSuccess) return attr[dev];
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  k_gemm_tf32x3<<<grid, NTHREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, C, ldc, M, N, K, err);
+  return cudaGetLastError();
+}
+
+}  // namespace tc
+}  // namespace mpsvqe
+
+// ------------------------------------------------------------------ C ABI
+#include "../../include/mpsvqe.h"
+
+extern "C" int mps_tc_gemm_tf32x3(int M, int N, int K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                                  float* C, int64_t ldc, void* cuda_stream) {
+  using namespace mpsvqe;
+  if (M < 0 || N < 0 || K < 1 || !A || !B || !C || lda < K || ldb < K || ldc < N) {
+    set_error_message("mps_tc_gemm_tf32x3: needs M, N >= 0, K >= 1, lda, ldb >= K, ldc >= N and non-null pointers");
+    return MPS_EINVAL;
+  }
+  if (M == 0 || N == 0) return MPS_OK;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int64_t ldk = ((int64_t)K + 3) & ~(int64_t)3;
+  float* buf = nullptr;
+  int* err = nullptr;
+  const size_t na = (size_t)M * ldk, nb = (size_t)N * ldk;
+  if (cudaMallocAsync((void**)&buf, (2 * na + 2 * nb) * sizeof(float), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&err, sizeof(int), st) != cudaSuccess) {
+    set_error_message("mps_tc_gemm_tf32x3: cudaMallocAsync of the split planes failed");
+    return MPS_ENOMEM;
+  }
+  int rc = MPS_OK;
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = tc::launch_split_tf32(A, lda, M, K, buf, buf + na, ldk, st);
+  if (e == cudaSuccess) e = tc::launch_split_tf32(B, ldb, N, K, buf + 2 * na, buf + 2 * na + nb, ldk, st);
+  if (e == cudaSuccess)
+    e = tc::launch_gemm_tf32x3(tc::SplitPlane{buf, buf + na, ldk}, tc::SplitPlane{buf + 2 * na, buf + 2 * na + nb, ldk},
+                               M, N, K, C, ldc, err, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(buf, st);
+  cudaFreeAsync(err, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_error_message((std::string("mps_tc_gemm_tf32x3: ") + cudaGetErrorString(e)).c_str());
+    rc = MPS_ECUDA;
+  } else if (herr) {
+    set_error_message("mps_tc_gemm_tf32x3: a bounded tensor-core pipeline wait ran out");
+    rc = MPS_ETIMEOUT;
+  }
+  return rc;
+}

@@ -9,6 +9,12 @@ computed by the same deterministic kernels as a lone call, so it does not depend
 else is in flight. A request can be cancelled (Future.cancel) until it starts running.
 Latencies (submit to result) give p50/p99 beside the throughput.
 
+First fit lets small requests pass a large one that does not fit yet; so that a steady
+stream of small requests cannot starve it, once the oldest queued request has waited
+longer than max_wait_s nothing behind it is admitted until it fits (head-of-line
+reservation). Handles take and return device memory stream-ordered on their own stream,
+so a request that finishes does not wait for the launches of the others.
+
 The host objects of a request (Jordan-Wigner Hamiltonian with its prefix trie, compiled
 circuit) are built at submission, because the device-memory estimate needs their sizes.
 """
@@ -63,11 +69,14 @@ class _Item:
 
 class Server:
     """budget_bytes: device bytes the loop may hand out (default: 80 % of the free device
-    memory at construction); max_inflight: requests running at once. run_fn replaces the
-    device execution (host-logic tests); it receives the request and returns its value."""
+    memory at construction); max_inflight: requests running at once; max_wait_s: queue
+    age after which the oldest request reserves the head of the line. run_fn replaces
+    the device execution (host-logic tests); it receives the request and returns its
+    value."""
 
-    def __init__(self, budget_bytes=None, max_inflight=16, device=0, run_fn=None):
+    def __init__(self, budget_bytes=None, max_inflight=16, device=0, run_fn=None, max_wait_s=30.0):
         self._run_fn = run_fn
+        self.max_wait_s = float(max_wait_s)
         self._device = device
         if budget_bytes is None:
             import torch
@@ -122,15 +131,23 @@ class Server:
                         self._queue.remove(it)          # cancelled while queued
                     if self.inflight < self.max_inflight:
                         room = self.budget - self.used
-                        for it in list(self._queue):
+                        now = time.perf_counter()
+                        for i, it in enumerate(list(self._queue)):
                             if self.inflight + len(picked) >= self.max_inflight:
                                 break
                             if it.need <= room:
                                 picked.append(it)
                                 room -= it.need
+                            elif i == 0 and now - it.t_submit > self.max_wait_s:
+                                break       # the starving head keeps the room it waits for
                     if picked:
                         break
-                    self._cv.wait()
+                    # wake up again when the head of the queue reaches its age limit
+                    timeout = None
+                    if self._queue:
+                        timeout = max(0.001, self._queue[0].t_submit + self.max_wait_s - time.perf_counter()
+                                      + 0.001)
+                    self._cv.wait(timeout)
                 for it in picked:
                     self._queue.remove(it)
                     self.used += it.need
@@ -181,6 +198,11 @@ class Server:
             it.future.set_exception(err)
 
     # ------------------------------------------------------------------ reporting
+    def records(self):
+        """(t_submit, t_start, t_done, kind) of every completed request."""
+        with self._cv:
+            return list(self._records)
+
     def stats(self):
         with self._cv:
             rec = list(self._records)

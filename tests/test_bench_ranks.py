@@ -37,5 +37,6 @@ def test_max_over_ranks_gloo_world_2():
 
 
 def test_replica_rate_counts_every_rank():
-    assert bench.replica_rate(1, 500.0) == pytest.approx(2.0)
-    assert bench.replica_rate(4, 500.0) == pytest.approx(8.0)
+    assert bench.replica_rate(1, 1, 0.5) == pytest.approx(2.0)
+    assert bench.replica_rate(4, 1, 0.5) == pytest.approx(8.0)
+    assert bench.replica_rate(2, 20, 300.0) == pytest.approx(40 / 300.0)

@@ -19,7 +19,12 @@ from paper_2207_03711_gb300 import synthetic as syn
 pytestmark = pytest.mark.gpu
 
 FP64_E_TOL = 1e-9       # Ha, FP64 path vs oracle on a unique result
-MIXED_E_TOL = 2e-4      # Ha, mixed path (complex64, FP32 SVD) on 8-10 qubit problems
+# Ha, mixed path (complex64 tensors, FP32 SVD with a compensated re-orthonormalisation)
+# on the untruncated cases: the 1e-6 target at 8 qubits (1568 gates); at 10 qubits
+# (~10^4 gates) complex64 storage alone already costs ~1e-6 (an FP64 SVD on complex64
+# tensors reaches 1.1e-6 on these inputs), so the bound stated there is 3e-6
+MIXED_E_TOL_8Q = 1e-6
+MIXED_E_TOL_10Q = 3e-6
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -81,7 +86,7 @@ def test_uccsd_8q_mixed_energy(uccsd8):
     M = G.mps_create(c["n"], c["chi"], G.MPS_MIXED)
     e = G.vqe_energy(M, C, H, c["theta"])
     print(f"8-qubit mixed |dE| = {abs(e - c['e2']):.3e} Ha")
-    assert abs(e - c["e2"]) <= MIXED_E_TOL
+    assert abs(e - c["e2"]) <= MIXED_E_TOL_8Q
 
 
 @pytest.mark.parametrize("prec", [G.MPS_FP64, G.MPS_MIXED])
@@ -116,7 +121,7 @@ def test_untruncated_10q_matches_statevector(prec):
         assert G.mps_get_stats(M)["discarded_weight"] < 1e-11
         assert abs(e - e1) <= FP64_E_TOL
     else:
-        assert abs(e - e1) <= MIXED_E_TOL
+        assert abs(e - e1) <= MIXED_E_TOL_10Q
 
 
 # -------------------------------------------------- single truncated steps, 24 q
@@ -204,10 +209,14 @@ def test_measurement_parity_full_size():
     ref = np.array([mps.expect_string(st, codes[i]) for i in idx]) / nrm
     assert np.abs(vals[idx] - ref).max() <= 1e-11
     assert np.abs(vals.imag).max() <= 1e-11
-    # the energy of the loaded state through the FP64 sum kernel: apply no gates
-    H = G.ham_create(codes, coeffs)
-    e_terms = sv.neumaier_sum(list(coeffs * vals.real))
-    assert np.isfinite(e_terms)
+    # the energy of the loaded entangled state through the library's own trie
+    # measurement and FP64 compensated sum, against the oracle's plain contraction of
+    # every string
+    H = G.ham_jw_from_integrals(h, g)
+    e_gpu = G.mps_energy(M, H)
+    e_ref, _ = mps.energy(st, codes, coeffs)
+    print(f"24q chi64 loaded-state energy |dE| = {abs(e_gpu - e_ref):.3e} Ha")
+    assert abs(e_gpu - e_ref) <= FP64_E_TOL
     H.close()
 
 

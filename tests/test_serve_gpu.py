@@ -49,9 +49,15 @@ def test_results_alone_equal_results_in_the_mix():
         futs = [srv.submit(r) for r in reqs]
         mixed = [f.result(timeout=600) for f in futs]
         st = srv.stats()
+        rec = srv.records()
     for a, b in zip(alone, mixed):
         assert np.array_equal(np.asarray(a), np.asarray(b))
     assert st["completed"] == len(reqs)
     assert st["peak_used_bytes"] <= budget
     assert st["peak_inflight"] >= 2
     assert st["latency_p99_s"] >= st["latency_p50_s"] > 0
+    # continuous, not in waves: some request started after another one and finished
+    # while that one was still running (its handle came and went mid-launch)
+    nested = [(a, b) for a in rec for b in rec if a[1] < b[1] and b[2] < a[2]]
+    print(f"{len(nested)} nested request intervals of {len(rec)} requests")
+    assert nested

@@ -95,3 +95,31 @@ def test_cancelled_request_never_runs():
         assert f1.cancelled()
         st = srv.stats()
     assert 1 not in ran and st["completed"] == 2
+
+
+def test_large_request_is_not_starved_by_a_stream_of_small_ones():
+    """Budget 100: a request needing 70 never fits next to the small ones (40 each) that
+    keep arriving; after max_wait_s it reserves the head of the line and completes while
+    the small stream is still arriving."""
+    stop = threading.Event()
+
+    def run(req):
+        time.sleep(0.02)
+        return req.tag
+
+    with Server(budget_bytes=100, max_inflight=4, run_fn=run, max_wait_s=0.1) as srv:
+        first = [srv.submit(_req(100 + i), need_bytes=40) for i in range(2)]   # fill the budget
+        big = srv.submit(_req(0), need_bytes=70)
+
+        def feeder():
+            i = 0
+            while not stop.is_set():
+                srv.submit(_req(200 + i), need_bytes=40)
+                i += 1
+                time.sleep(0.005)
+        t = threading.Thread(target=feeder, daemon=True)
+        t.start()
+        assert big.result(timeout=3) == 0
+        stop.set()
+        t.join()
+        assert all(f.result(timeout=5) >= 100 for f in first)
