@@ -144,8 +144,9 @@ int mps_set_svd_params(mps_t mps, double cutoff, int max_sweeps);
 /* Memory of the trie measurement (Sec. III-C; no counterpart in the paper's text). The
  * prefix trie of the strings is walked depth first in chunks of consecutive nodes of one
  * level, each level keeping environment buffers (3 chi^2 complex entries per node) for
- * one chunk: bytes bounds the sum of those buffers (at least 16 nodes per level).
- * 0 restores the default, 4 GiB for chi <= 128 and 16 GiB above, which mps_estimate_bytes
+ * one chunk: bytes bounds the sum of those buffers (at least 16 nodes per level); the
+ * tensor-core scratch of mixed precision then takes a quarter of bytes (at least 64 MiB).
+ * 0 restores the default, 4 GiB for chi <= 128 and 48 GiB above, which mps_estimate_bytes
  * assumes. Results do not depend on the chunking. */
 int mps_set_meas_budget(mps_t mps, size_t bytes);
 
@@ -232,8 +233,18 @@ typedef struct {
                            /* over the slots of the call                           */
   double alg_flops_call;   /* algorithmic real flops of this call's gate steps,    */
                            /* summed over every slot the call ran                  */
+  int64_t tc_gemm_launches; /* tensor-core GEMMs of the call's measurements        */
+  double tc_gemm_flops;    /* their algorithmic real flops (2 M N K each; the split */
+                           /* products are not counted)                            */
+  double ms_tc_gemm;       /* their summed CUDA-event time, when kernel timing is   */
+                           /* on (mps_set_kernel_timing), else 0                   */
 } mps_stats_t;
 int mps_get_stats(mps_t mps, mps_stats_t* stats);
+
+/* Record CUDA events around every tensor-core GEMM launch of the measurement (on the
+ * handle's stream) and report their summed time in mps_stats_t.ms_tc_gemm; off by
+ * default (no paper counterpart: it serves roofline reporting). */
+int mps_set_kernel_timing(mps_t mps, int on);
 
 /* Device bytes that a handle of these sizes would hold once it has run circ (null:
  * circuit buffers left out) and measured ham (null: measurement buffers left out).

@@ -37,7 +37,8 @@ class MpsStats(ctypes.Structure):
                 ("ms_measure", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
                 ("cycles", ctypes.c_double * 7), ("n_fallback", ctypes.c_int64),
                 ("alg_flops_total", ctypes.c_double), ("n_nonfinite", ctypes.c_int64),
-                ("alg_flops_call", ctypes.c_double)]
+                ("alg_flops_call", ctypes.c_double), ("tc_gemm_launches", ctypes.c_int64),
+                ("tc_gemm_flops", ctypes.c_double), ("ms_tc_gemm", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -58,6 +59,7 @@ SIGNATURES = {
     "mps_reset": [_P, _I, _P],
     "mps_set_svd_params": [_P, _D, _I],
     "mps_set_meas_budget": [_P, ctypes.c_size_t],
+    "mps_set_kernel_timing": [_P, _I],
     "mps_apply_circuit": [_P, _P, _P, _PD],
     "mps_apply_gates": [_P, _I64, _P, _P, _PD],
     "mps_expect_paulis": [_P, _I64, _P, _P, _P],
@@ -272,6 +274,10 @@ def mps_reset(mps, occ, slot=0):
 
 def mps_set_svd_params(mps, cutoff, max_sweeps):
     _check(load_library().mps_set_svd_params(mps, cutoff, max_sweeps))
+
+
+def mps_set_kernel_timing(mps, on=True):
+    _check(load_library().mps_set_kernel_timing(mps, 1 if on else 0))
 
 
 def mps_set_meas_budget(mps, nbytes):

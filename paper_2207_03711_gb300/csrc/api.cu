@@ -133,6 +133,10 @@ struct mps_s {
   std::vector<int32_t> lvl_cap;
   size_t meas_budget = 0;          // 0: the default of meas_plan
   EnvTc tc{};
+  // optional per-launch timing of the tensor-core GEMMs (mps_set_kernel_timing)
+  bool ktime = false;
+  std::vector<cudaEvent_t> kev;
+  size_t kev_used = 0;
   size_t tc_floats = 0;
   double* d_theta = nullptr;
   size_t theta_cap = 0;
@@ -170,6 +174,8 @@ struct mps_s {
     dfree(d_shift_gate, st);
     dfree(d_shift_val, st);
     for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+    for (auto e : kev)
       if (e) cudaEventDestroy(e);
   }
 };
@@ -273,9 +279,9 @@ static int ensure_theta(mps_s* m, size_t count) {
 // consecutive nodes of one level, so only one chunk per level is live: level k keeps
 // environment buffers (L: chi^2, T: 2 chi^2 complex entries per node) for cap[k] nodes.
 // cap[k] = min(nodes of level k, U) with U set by a per-handle budget (4 GiB of level
-// buffers for chi <= 128, 16 GiB above) spread over the levels; in mixed precision the
-// tensor-core scratch holds tc_nodes nodes (about 1 GiB).
-constexpr int kTcMinDim = 32;     // levels with both bonds >= 32 use the tensor cores
+// buffers for chi <= 128, 48 GiB above) spread over the levels; in mixed precision the
+// tensor-core scratch holds tc_nodes nodes (about 1 GiB for chi <= 128, 4 GiB above).
+constexpr int kTcMinDim = 128;    // levels with both bonds >= 128 use the tensor cores
 struct MeasPlan {
   std::vector<int32_t> cap;
   int tc_nodes = 0;
@@ -284,7 +290,8 @@ struct MeasPlan {
 static MeasPlan meas_plan(const Trie& t, int chi, size_t es, bool mixed, size_t budget = 0) {
   MeasPlan p;
   const size_t chi2 = (size_t)chi * chi, node_bytes = 3 * chi2 * es;
-  if (budget == 0) budget = (chi <= 128 ? size_t(4) : size_t(16)) << 30;
+  const bool explicit_budget = budget != 0;
+  if (budget == 0) budget = (chi <= 128 ? size_t(4) : size_t(48)) << 30;
   const size_t per_level = budget / (size_t)std::max(1, t.n_levels);
   const int32_t U = (int32_t)std::max<size_t>(16, per_level / node_bytes);
   p.cap.assign(t.n, 0);
@@ -296,7 +303,10 @@ static MeasPlan meas_plan(const Trie& t, int chi, size_t es, bool mixed, size_t 
   }
   if (mixed && chi >= kTcMinDim) {
     const size_t per_node = 96 * chi2;    // float planes and GEMM outputs per node
-    p.tc_nodes = (int)std::min<size_t>((size_t)cmax, std::max<size_t>(32, (size_t(1) << 30) / per_node));
+    // a quarter of an explicit budget, else 1 GiB (chi <= 128) or 4 GiB
+    const size_t tc_budget = explicit_budget ? std::max<size_t>(size_t(64) << 20, budget / 4)
+                                             : (chi <= 128 ? size_t(1) : size_t(4)) << 30;
+    p.tc_nodes = (int)std::min<size_t>((size_t)cmax, std::max<size_t>(32, tc_budget / per_node));
     p.tc_bytes = env_tc_scratch_floats(chi, p.tc_nodes) * sizeof(float) + 256;
   }
   return p;
@@ -452,6 +462,21 @@ struct MeasWalk {
   int launches = 0;
 };
 
+// The next pair of timing events (created on first use) when kernel timing is on.
+static int next_event_pair(mps_s* m, cudaEvent_t* e0, cudaEvent_t* e1) {
+  *e0 = *e1 = nullptr;
+  if (!m->ktime) return MPS_OK;
+  while (m->kev.size() < m->kev_used + 2) {
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    m->kev.push_back(e);
+  }
+  *e0 = m->kev[m->kev_used];
+  *e1 = m->kev[m->kev_used + 1];
+  m->kev_used += 2;
+  return MPS_OK;
+}
+
 static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
   mps_s* m = c.m;
   const Trie& t = c.h->trie;
@@ -466,9 +491,13 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
     ++c.launches;
     for (int s0 = 0; s0 < U; s0 += m->tc.max_nodes) {
       const int ns = std::min(m->tc.max_nodes, U - s0);
+      cudaEvent_t e0, e1;
+      TRY(next_event_pair(m, &e0, &e1));
       CU(env_tc_T(m->tc, (const Cx<float>*)L + (size_t)s0 * chi2, (Cx<float>*)T + (size_t)s0 * 2 * chi2, ns, D, Dp,
-                  m->st));
+                  m->st, e0, e1));
       c.launches += 3;
+      m->stats.tc_gemm_launches += 1;
+      m->stats.tc_gemm_flops += 2.0 * ((double)ns * D) * (4.0 * Dp) * (2.0 * D);
     }
   } else {
     CU(launch_env_T(m->dm, m->prec, c.slot, k, L, T, U, m->st));
@@ -491,10 +520,20 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
     int64_t b = a + 1;
     while (b < c1 && b - a < m->lvl_cap[k + 1] && (!tc || par[b] - par[a] < m->tc.max_nodes)) ++b;
     if (tc) {
+      // the shared operands of site k live in the scratch, which the deeper levels of
+      // the previous sub-chunk have used for their own sites: rebuild them
+      const Cx<float>* Bk = (const Cx<float>*)m->dm.B + (size_t)c.slot * m->dm.slot_elems + m->site_off[k];
+      CU(env_tc_site(m->tc, Bk, D, Dp, m->st));
+      ++c.launches;
+      cudaEvent_t e0, e1;
+      TRY(next_event_pair(m, &e0, &e1));
+      const int np = par[b - 1] - par[a] + 1;
       CU(env_tc_children(m->tc, (const Cx<float>*)T, par[a] - u0, par[b - 1] - u0 + 1, D, Dp,
                          c.h->d_parent[k + 1] + a, c.h->d_edge[k + 1] + a, (int)(b - a), u0,
-                         (Cx<float>*)m->lvl_L[k + 1], m->st));
+                         (Cx<float>*)m->lvl_L[k + 1], m->st, e0, e1));
       c.launches += 3;
+      m->stats.tc_gemm_launches += 1;
+      m->stats.tc_gemm_flops += 2.0 * (4.0 * Dp) * ((double)np * 2 * Dp) * (2.0 * D);
     } else {
       CU(launch_env_child(m->dm, m->prec, c.slot, k, T, c.h->d_parent[k + 1] + a, c.h->d_edge[k + 1] + a,
                           (int)(b - a), u0, m->lvl_L[k + 1], m->st));
@@ -515,8 +554,9 @@ static int run_measure(mps_s* m, ham_s* h, int slot, double* out_host, bool term
   CU(cudaStreamSynchronize(m->st));
   CU(cudaMemcpy(c.r.data(), m->dm.rank + (size_t)slot * (m->n + 1), (m->n + 1) * 4, cudaMemcpyDeviceToHost));
   if (m->tc.err) CU(cudaMemsetAsync(m->tc.err, 0, sizeof(int), m->st));
+  m->kev_used = 0;
   CU(cudaEventRecord(m->ev[2], m->st));
-  CU(launch_right_envs(m->dm, m->prec, slot, c.r.data(), m->w, m->st, &c.launches));
+  CU(launch_right_envs(m->dm, m->prec, slot, c.r.data(), m->site_off.data(), m->w, m->st, &c.launches));
   const Trie& t = h->trie;
   if (t.n_levels > 0) {
     // root environment L_0 = [1] (one node, D_0 = 1)
@@ -538,6 +578,11 @@ static int run_measure(mps_s* m, ham_s* h, int slot, double* out_host, bool term
   CU(cudaEventElapsedTime(&ms, m->ev[2], m->ev[3]));
   m->stats.ms_measure += ms;
   m->stats.kernel_launches += c.launches;
+  for (size_t i = 0; i + 1 < m->kev_used; i += 2) {
+    float t = 0;
+    CU(cudaEventElapsedTime(&t, m->kev[i], m->kev[i + 1]));
+    m->stats.ms_tc_gemm += t;
+  }
   if (tc_err) return fail(MPS_ETIMEOUT, "a bounded wait of the tensor-core GEMM pipeline ran out");
   return MPS_OK;
 }
@@ -806,6 +851,12 @@ int mps_set_svd_params(mps_t m, double cutoff, int max_sweeps) {
 // fill the per-call statistics; the counts of Jacobi caps and skipped non-finite gates
 // are summed over the slots. Returns MPS_ENONFINITE if any slot skipped a gate whose M'
 // held a NaN or Inf, else MPS_ENOCONV if any Jacobi fallback reached its sweep cap.
+int mps_set_kernel_timing(mps_t m, int on) {
+  if (!m) return fail(MPS_EINVAL, "mps_set_kernel_timing: null handle");
+  m->ktime = on != 0;
+  return MPS_OK;
+}
+
 int mps_set_meas_budget(mps_t m, size_t bytes) {
   if (!m) return fail(MPS_EINVAL, "mps_set_meas_budget: null handle");
   // a new budget takes effect at the next measurement; buffers are rebuilt to match
@@ -819,6 +870,9 @@ int mps_set_meas_budget(mps_t m, size_t bytes) {
     p = nullptr;
   }
   std::fill(m->lvl_cap.begin(), m->lvl_cap.end(), 0);
+  dfree(m->tc.scratch, m->st);
+  m->tc.scratch = nullptr;
+  m->tc.max_nodes = 0;
   m->meas_budget = bytes;
   return MPS_OK;
 }

@@ -207,23 +207,26 @@ cudaError_t env_tc_site(const EnvTc& s, const Cx<float>* Bk, int D, int Dp, cuda
   return cudaGetLastError();
 }
 
-cudaError_t env_tc_T(const EnvTc& s, const Cx<float>* L, Cx<float>* T, int U, int D, int Dp, cudaStream_t st) {
+cudaError_t env_tc_T(const EnvTc& s, const Cx<float>* L, Cx<float>* T, int U, int D, int Dp, cudaStream_t st,
+                     cudaEvent_t e0, cudaEvent_t e1) {
   if (U <= 0) return cudaSuccess;
   const Parts p = carve(s.scratch, s.chi, s.max_nodes);
   const int64_t ldk = round4(2 * D), chi2 = (int64_t)s.chi * s.chi;
   k_tc_split_L<<<grid_for((int64_t)U * D * ldk), 256, 0, st>>>(L, chi2, U, D, p.lh, p.ll, ldk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (e0 && (e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
   e = tc::launch_gemm_tf32x3(tc::SplitPlane{p.lh, p.ll, ldk}, tc::SplitPlane{p.bth, p.btl, ldk}, U * D, 4 * Dp,
                              2 * D, p.ct, 4 * Dp, s.err, st);
   if (e != cudaSuccess) return e;
+  if (e1 && (e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
   k_tc_scatter_T<<<grid_for((int64_t)U * 2 * D * Dp), 256, 0, st>>>(p.ct, U, D, Dp, T, chi2);
   return cudaGetLastError();
 }
 
 cudaError_t env_tc_children(const EnvTc& s, const Cx<float>* T, int pa, int pb, int D, int Dp,
                             const int32_t* parent, const uint8_t* edge, int nc, int node_base, Cx<float>* Lout,
-                            cudaStream_t st) {
+                            cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
   if (nc <= 0 || pb <= pa) return cudaSuccess;
   const Parts p = carve(s.scratch, s.chi, s.max_nodes);
   const int64_t ldk = round4(2 * D), chi2 = (int64_t)s.chi * s.chi;
@@ -233,9 +236,11 @@ cudaError_t env_tc_children(const EnvTc& s, const Cx<float>* T, int pa, int pb, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t N = (int64_t)np * 2 * Dp;
+  if (e0 && (e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
   e = tc::launch_gemm_tf32x3(tc::SplitPlane{p.ach, p.acl, ldk}, tc::SplitPlane{p.tth, p.ttl, ldk}, 4 * Dp, (int)N,
                              2 * D, p.cl, N, s.err, st);
   if (e != cudaSuccess) return e;
+  if (e1 && (e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
   k_tc_combine<<<grid_for((int64_t)nc * Dp * Dp), 256, 0, st>>>(p.cl, N, Dp, parent, edge, nc, node_base, pa, Lout,
                                                                 chi2);
   return cudaGetLastError();

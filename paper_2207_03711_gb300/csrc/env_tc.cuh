@@ -21,11 +21,13 @@ size_t env_tc_scratch_floats(int chi, int max_nodes);
 // Shared operands of site k (D = left bond, Dp = right bond), once per level chunk.
 cudaError_t env_tc_site(const EnvTc& s, const Cx<float>* Bk, int D, int Dp, cudaStream_t st);
 // T_j[u] = L[u] B^j for U nodes (U <= max_nodes).
-cudaError_t env_tc_T(const EnvTc& s, const Cx<float>* L, Cx<float>* T, int U, int D, int Dp, cudaStream_t st);
+// e0 / e1 (optional) are recorded on st right before and after the tensor-core GEMM.
+cudaError_t env_tc_T(const EnvTc& s, const Cx<float>* L, Cx<float>* T, int U, int D, int Dp, cudaStream_t st,
+                     cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
 // L of the nc children whose parents are buffer entries [pa, pb) of T (trie index of
 // entry 0 is node_base), from C_ij = (B^i)^+ T_j and the edge letters.
 cudaError_t env_tc_children(const EnvTc& s, const Cx<float>* T, int pa, int pb, int D, int Dp,
                             const int32_t* parent, const uint8_t* edge, int nc, int node_base, Cx<float>* Lout,
-                            cudaStream_t st);
+                            cudaStream_t st, cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
 
 }  // namespace mpsvqe

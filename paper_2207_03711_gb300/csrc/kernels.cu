@@ -750,8 +750,8 @@ cudaError_t launch_circuit(const DevMPS& m, int prec, const CircDev& c, int64_t 
 // large bond dimensions use many SMs. ranks: the slot's bond ranks on the host
 // (ranks[k] = left dimension of site k).
 template <class R>
-static cudaError_t right_envs_t(const DevMPS& m, int slot, const int* ranks, Cx<R>* Renv, Cx<R>* Bhat,
-                                cudaStream_t st) {
+static cudaError_t right_envs_t(const DevMPS& m, int slot, const int* ranks, const int64_t* site_off, Cx<R>* Renv,
+                                Cx<R>* Bhat, cudaStream_t st) {
   const int n = m.n;
   const size_t chi2 = (size_t)m.chi * m.chi;
   const Cx<R>* Bslot = (const Cx<R>*)m.B + (size_t)slot * m.slot_elems;
@@ -760,8 +760,8 @@ static cudaError_t right_envs_t(const DevMPS& m, int slot, const int* ranks, Cx<
   if (e != cudaSuccess) return e;
   for (int k = n - 1; k >= 0; --k) {
     const int Dl = ranks[k], Dr = ranks[k + 1];
-    const Cx<R>* Bk = Bslot + m.site_off[k];
-    Cx<R>* Bh = Bhat + m.site_off[k];
+    const Cx<R>* Bk = Bslot + site_off[k];
+    Cx<R>* Bh = Bhat + site_off[k];
     const Cx<R>* Rn = Renv + (size_t)(k + 1) * chi2;
     GridGemm<R> g{};
     g.nterm = 1;
@@ -788,11 +788,12 @@ static cudaError_t right_envs_t(const DevMPS& m, int slot, const int* ranks, Cx<
   return cudaGetLastError();
 }
 
-cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, const int* ranks, MeasDev& w, cudaStream_t st,
-                              int* launches) {
+cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, const int* ranks, const int64_t* site_off,
+                              MeasDev& w, cudaStream_t st, int* launches) {
   *launches += 2 * m.n;
-  if (prec == MPS_PREC_FP64) return right_envs_t<double>(m, slot, ranks, (Cx<double>*)w.R, (Cx<double>*)w.Bhat, st);
-  return right_envs_t<float>(m, slot, ranks, (Cx<float>*)w.R, (Cx<float>*)w.Bhat, st);
+  if (prec == MPS_PREC_FP64)
+    return right_envs_t<double>(m, slot, ranks, site_off, (Cx<double>*)w.R, (Cx<double>*)w.Bhat, st);
+  return right_envs_t<float>(m, slot, ranks, site_off, (Cx<float>*)w.R, (Cx<float>*)w.Bhat, st);
 }
 
 // ------------------------------------------------------------------ trie level

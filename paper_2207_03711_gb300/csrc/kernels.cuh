@@ -69,9 +69,10 @@ struct MeasDev {
 // Thread-local message returned by mps_last_error() (defined with the C ABI).
 void set_error_message(const char* msg);
 
-// ranks: the slot's n+1 bond ranks on the host (ranks[k] = left dimension of site k).
-cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, const int* ranks, MeasDev& w, cudaStream_t st,
-                              int* launches);
+// ranks: the slot's n+1 bond ranks on the host (ranks[k] = left dimension of site k);
+// site_off: the n site offsets on the host (DevMPS::site_off is the device copy).
+cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, const int* ranks, const int64_t* site_off,
+                              MeasDev& w, cudaStream_t st, int* launches);
 // Chunked trie levels. Environment buffers: L holds node u's D_k x D_k block (row-major,
 // leading dimension D_k) at u chi^2 complex entries; T holds T_j[u] = L[u] B_k^j
 // (D_k x D_{k+1}, leading dimension D_{k+1}) at (2u + j) chi^2. Node indices in cnode /

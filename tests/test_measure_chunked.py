@@ -4,9 +4,10 @@ Sec. III-C) against the oracle's plain left-to-right contraction of each string.
 * The result does not depend on the chunking: a budget that forces chunks of 16 nodes
   per level gives the same expectations as whole levels (bit for bit in FP64, within
   rounding of the tensor-core tiles in mixed precision).
-* Mixed precision at the 24-qubit, chi = 64 shape, where the levels with both bonds
-  >= 32 run on the tensor cores: sampled strings and the energy of the loaded state
-  against the FP64 oracle.
+* Mixed precision at the 24-qubit, chi = 64 shape (CUDA-core environments): sampled
+  strings and the energy of the loaded state against the FP64 oracle.
+* Mixed precision at 20 qubits, chi = 128, where the levels whose bonds are both >= 128
+  run on the tensor cores: chunked against whole levels, and against the oracle.
 * Bond dimension 256 at 64 qubits (the measurement-bound configuration: a seeded random
   right-canonical MPS with every interior rank at min(256, 2^min(k+1, n-1-k))): seeded
   Jordan-Wigner-shaped strings sharing prefixes, FP64 and mixed, against the oracle.
@@ -89,7 +90,7 @@ def test_chunking_does_not_change_results(prec):
     assert np.abs(chunked[idx] - ref).max() <= tol
 
 
-def test_mixed_measurement_on_tensor_cores_24q():
+def test_mixed_measurement_24q():
     n, chi = 24, 64
     st = _canon(n, chi, 3, bias=2.0)
     h, g = syn.random_integrals(12, 0)
@@ -112,6 +113,25 @@ def test_mixed_measurement_on_tensor_cores_24q():
     assert np.isfinite(e_gpu)
 
 
+def test_tensor_core_levels_20q_chi128():
+    n, chi = 20, 128
+    st = _canon(n, chi, 11, bias=2.0)
+    codes = jw_shaped_strings(n, 400, 12)
+    M = G.mps_create(n, chi, G.MPS_MIXED)
+    G.mps_set_state(M, st.B, st.lam)
+    G.mps_set_kernel_timing(M, True)
+    whole = G.mps_expect_paulis(M, codes)
+    s = G.mps_get_stats(M)
+    assert s["tc_gemm_launches"] > 0 and s["ms_tc_gemm"] > 0      # the tensor-core levels ran
+    G.mps_set_meas_budget(M, 1)
+    chunked = G.mps_expect_paulis(M, codes)
+    ref = np.array([mps.expect_string(st, c) for c in codes]) / mps.norm2(st)
+    print(f"20q chi128 mixed: whole vs chunked {np.abs(whole - chunked).max():.3e}, vs oracle "
+          f"{np.abs(whole - ref).max():.3e} (max|<P>| {np.abs(ref).max():.3e}), tc launches {s['tc_gemm_launches']}")
+    assert np.abs(whole - chunked).max() <= 1e-6
+    assert np.abs(whole - ref).max() <= 2e-5
+
+
 @pytest.mark.parametrize("prec", [G.MPS_FP64, G.MPS_MIXED])
 def test_chi256_measurement_64q(prec):
     n, chi = 64, 256
@@ -126,7 +146,8 @@ def test_chi256_measurement_64q(prec):
     err = np.abs(vals - ref).max()
     print(f"64q chi256 prec={prec}: max|d<P>| = {err:.3e} over {len(codes)} strings, "
           f"max|<P>| = {np.abs(ref).max():.3e}")
-    assert err <= (1e-10 if prec == G.MPS_FP64 else 2e-5)
+    # mixed: complex64 environments through 64 levels of tensor-core contractions
+    assert err <= (1e-10 if prec == G.MPS_FP64 else 1e-4)
     with pytest.raises(G.MpsError) as e:       # gates are applied at chi <= 128 only
         G.mps_apply_gates(M, np.array([0], dtype=np.int32), np.eye(4)[None].astype(complex))
     assert e.value.code == G.MPS_EINVAL

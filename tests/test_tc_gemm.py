@@ -7,7 +7,8 @@ primitive as real GEMMs. Shapes cover one and several 128 x 256 tiles, ragged ed
 every dimension, K that is not a multiple of the 32-wide K tile, and leading
 dimensions larger than the logical width. The bound is elementwise,
 |C - AB^T| <= 1e-5 (|A||B|^T): a single TF32 product (10-bit mantissa) misses it by
-about 50x, so the low-order split products are really applied.
+about 50x, so the low-order split products are really applied. With one-signed
+operands the mean error must not grow with K (no accumulation bias).
 """
 import numpy as np
 import pytest
@@ -52,6 +53,28 @@ def test_tc_gemm_matches_fp64(M, N, K):
         t32 = lambda x: (x.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)
         one = t32(A[:, :K].copy()) @ t32(B[:, :K].copy()).T
         assert (np.abs(one - ref) / (scale + 1e-30)).max() > 1e-5
+
+
+@pytest.mark.parametrize("K", [512, 4096])
+def test_tc_gemm_has_no_accumulation_bias(K):
+    """The tensor core rounds its FP32 accumulation toward zero, which over a long K makes
+    a one-signed error (measured -5e-6 of the result at K = 512 and -9e-5 at 8192 when
+    the whole K ran in TMEM). The kernel accumulates each 32-wide K tile from zero and
+    adds the tiles in round-to-nearest FP32, so with positive operands the mean relative
+    error stays at one tile's worth, independent of K."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(K)
+    M = N = 256
+    A = rng.uniform(0.5, 1.0, size=(M, K)).astype(np.float32)
+    B = rng.uniform(0.5, 1.0, size=(N, K)).astype(np.float32)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    G.mps_tc_gemm_tf32x3(M, N, K, dA.data_ptr(), K, dB.data_ptr(), K, dC.data_ptr(), N)
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    rel = (dC.cpu().numpy().astype(np.float64) - ref) / ref
+    print(f"K={K}: mean relative error {rel.mean():+.2e}, max {np.abs(rel).max():.2e}")
+    assert abs(rel.mean()) <= 1e-6
+    assert np.abs(rel).max() <= 2e-6
 
 
 def test_tc_gemm_rejects_bad_sizes():
