@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--config4-tc-case", action="store_true",
                     help="small profiling case of the tensor-core GEMM: one 64-qubit chi=256 measurement of "
                          "the first --case-strings strings")
+    ap.add_argument("--random-gates", action="store_true",
+                    help="second workload: random two-site gates in brickwork order on a random chi=128 MPS")
     ap.add_argument("--case-strings", type=int, default=2000)
     ap.add_argument("--case-budget-mb", type=int, default=0,
                     help="measurement buffer budget of the tensor-core case (0: the library default)")
@@ -543,6 +545,64 @@ def run_config4_tc_case(n_strings, budget_mb=0):
 
 
 
+def run_random_gates(args):
+    """The paper's second workload at the largest bond cap gates are applied at: random
+    two-site unitaries on neighbouring qubits (brickwork order) applied to a seeded random
+    right-canonical MPS of 32 qubits at chi = 128 (every interior rank 128 at the
+    centre), mixed precision. One step = 248 gates (eight brickwork layers) through
+    mps_apply_gates on one state; steps run back to back on the evolving state."""
+    import torch
+    import paper_2207_03711_gb300 as G
+    from paper_2207_03711_gb300 import synthetic as syn
+    G.build()
+    G.load_library()
+    n, chi = 32, 128
+    K, W = args.steps, max(3, args.warmup)
+    B, lam = syn.random_right_canonical_mps(n, chi, 1)
+    bonds = np.array(syn.brickwork_bonds(n, 8), dtype=np.int32)
+    Us = np.array([np.linalg.qr(z)[0] for z in syn.random_gate_matrices(len(bonds) * (K + W), 4)])
+    stream = torch.cuda.current_stream().cuda_stream
+    M = G.mps_create(n, chi, G.MPS_MIXED, cuda_stream=stream)
+    G.mps_set_state(M, B, lam)
+    ng = len(bonds)
+    for w in range(W):
+        G.mps_apply_gates(M, bonds, Us[w * ng:(w + 1) * ng], allow_noconv=True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    dev_ms, wall_ms, flops = [], [], []
+    for k in range(K):
+        o = (W + k) * ng
+        t0 = time.perf_counter()
+        G.mps_apply_gates(M, bonds, Us[o:o + ng], allow_noconv=True)
+        wall_ms.append((time.perf_counter() - t0) * 1e3)
+        s = G.mps_get_stats(M)
+        dev_ms.append(s["ms_circuit"])
+        flops.append(s["alg_flops_call"])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_dev = float(np.sum(dev_ms)) * 1e-3
+    peaks = alu_peaks(torch)
+    achieved = float(np.sum(flops)) / t_dev / 1e12
+    line = {"metric": "two-site gates/s", "value": K * ng / t_dev, "unit": "gates/s", "n_gpus": 1, "steps": K,
+            "warmup": W, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "random_brickwork_gates_32q_chi128", "qubits": n, "chi": chi,
+                       "gates_per_step": ng, "state": "seeded random right-canonical MPS, full ranks",
+                       "l2": "state (33 MB) L2-resident; the gate chain is serial"},
+            "e2e": {"value": K * ng / (float(np.sum(wall_ms)) * 1e-3), "unit": "gates/s",
+                    "h2d_bytes_per_step": int(ng * (4 + 256)), "d2h_bytes_per_step": 8 + 4 * 8},
+            "gpu_launches": int(s["kernel_launches"]),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp32_tflops"], "traffic": None,
+                         "peak_source": "measured: cuBLAS SGEMM in this process (FP32 CUDA cores)",
+                         "kernel": "k_circuit<float,512> (one thread block)",
+                         "frac_of_one_sm": achieved / (peaks["fp32_tflops"] / 152)},
+            "ms_per_gate": 1e3 * t_dev / (K * ng), "clocks": clocks}
+    print(json.dumps(line))
+
+
+
 def run_profile_case():
     """One gate-engine launch (256 gates of the 24-qubit circuit's interior on a saturated
     chi = 64 state) and one full measurement: a short, fixed workload for ncu."""
@@ -630,6 +690,8 @@ def main():
         return
     if args.config4:
         run_config4(args)
+    elif args.random_gates:
+        run_random_gates(args)
     elif args.config4_tc_case:
         run_config4_tc_case(args.case_strings, args.case_budget_mb)
     elif args.profile_case:

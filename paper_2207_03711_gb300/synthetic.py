@@ -78,3 +78,25 @@ def random_right_canonical_mps(n, chi, seed):
         l = np.sort(np.exp(-np.arange(r[b + 1]) / 8.0) * rng.uniform(0.5, 1.0, size=r[b + 1]))[::-1]
         lam.append(l / np.linalg.norm(l))
     return B, lam
+
+
+def mps_inspired_bonds(n):
+    """Bond pattern of the MPS-inspired circuit (unitaries that each entangle four
+    consecutive qubits, swept along the chain): for q = 0 .. n-4 a block of five two-site
+    gates on bonds q, q+1, q+2, q+1, q, i.e. one unitary on qubits q..q+3."""
+    return [b for q in range(n - 3) for b in (q, q + 1, q + 2, q + 1, q)]
+
+
+def brickwork_bonds(n, layers):
+    """Bonds of a brickwork of two-site gates on neighbouring qubits: even bonds, then odd
+    bonds, repeated."""
+    out = []
+    for layer in range(layers):
+        out += list(range(layer % 2, n - 1, 2))
+    return out
+
+
+def random_gate_matrices(count, seed):
+    """count complex Gaussian 4x4 matrices (the caller orthonormalises them, e.g. by QR)."""
+    rng = np.random.default_rng(50_000 + seed)
+    return rng.normal(size=(count, 4, 4)) + 1j * rng.normal(size=(count, 4, 4))

@@ -1,0 +1,98 @@
+"""The paper's second workload (Sec. III-A and Sec. IV-B): circuits of two-site gates
+other than UCCSD, checked against the oracle where the result is unique.
+
+* The MPS-inspired circuit: unitaries that each entangle four consecutive qubits, swept
+  along the chain (five random two-site gates per block). The state it makes has bond
+  dimension 8 exactly, so chi = 8 holds it without truncation: amplitudes against the
+  statevector at 12 qubits, Pauli expectations against the oracle's MPS at 40 qubits.
+* Random two-site gates in brickwork order on a random canonical MPS at bond cap 128 (the
+  paper's x86 comparison uses D = 512; gates are applied at chi <= 128 here): a short
+  prefix from an exact canonical state is unique, so Schmidt numbers and expectations
+  must agree.
+"""
+import numpy as np
+import pytest
+
+import paper_2207_03711_gb300 as G
+from oracle import circuit, mps
+from paper_2207_03711_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    G.build()
+    return G.load_library()
+
+
+def unitaries(count, seed):
+    return np.array([np.linalg.qr(z)[0] for z in syn.random_gate_matrices(count, seed)])
+
+
+@pytest.mark.parametrize("prec", [G.MPS_FP64, G.MPS_MIXED])
+def test_mps_inspired_circuit_12q_equals_statevector(prec):
+    n, chi = 12, 8
+    bonds = syn.mps_inspired_bonds(n)
+    Us = unitaries(len(bonds), 1)
+    psi = np.zeros(2 ** n, dtype=complex)
+    psi[0] = 1.0
+    for b, U in zip(bonds, Us):
+        psi = circuit.apply_two_site_sv(psi, b, U, n)
+    M = G.mps_create(n, chi, prec)
+    G.mps_reset(M, [0] * n)
+    dw = G.mps_apply_gates(M, np.array(bonds, dtype=np.int32), Us)
+    r, sites, lams = G.mps_get_state(M)
+    assert list(r) == [2, 4, 8, 8, 8, 8, 8, 8, 8, 4, 2]
+    got = mps.to_statevector(mps.MPS(sites, lams))
+    err = np.abs(got - psi).max()
+    print(f"MPS-inspired 12q prec={prec}: max|d psi| = {err:.3e}, discarded {dw:.2e}")
+    if prec == G.MPS_FP64:
+        assert err <= 1e-12 and dw < 1e-20
+    else:
+        assert err <= 2e-6
+
+
+def test_mps_inspired_circuit_40q_expectations():
+    n, chi = 40, 8
+    bonds = syn.mps_inspired_bonds(n)
+    Us = unitaries(len(bonds), 2)
+    st = mps.hf_mps(n, 0)
+    mps.apply_gates(st, list(zip(bonds, Us)), chi)
+    M = G.mps_create(n, chi, G.MPS_FP64)
+    G.mps_reset(M, [0] * n)
+    G.mps_apply_gates(M, np.array(bonds, dtype=np.int32), Us)
+    assert list(G.mps_get_ranks(M)) == st.ranks()
+    rng = np.random.default_rng(3)
+    codes = rng.integers(0, 4, size=(60, n)).astype(np.uint8)
+    codes[:, 10:] = np.where(rng.random((60, n - 10)) < 0.8, 0, codes[:, 10:])   # mostly local strings
+    vals = G.mps_expect_paulis(M, codes)
+    ref = np.array([mps.expect_string(st, c) for c in codes]) / mps.norm2(st)
+    print(f"MPS-inspired 40q: max|d<P>| = {np.abs(vals - ref).max():.3e}, max|<P>| = {np.abs(ref).max():.3e}")
+    assert np.abs(vals - ref).max() <= 1e-11
+
+
+@pytest.mark.parametrize("prec", [G.MPS_FP64, G.MPS_MIXED])
+def test_random_brickwork_gates_chi128_prefix(prec):
+    n, chi = 20, 128
+    r = syn.full_ranks(n, chi)
+    st = mps.random_canonical(n, r, syn.random_mps_gaussians(n, r, 6))
+    bonds = syn.brickwork_bonds(n, 2)[:12]
+    Us = unitaries(len(bonds), 7)
+    M = G.mps_create(n, chi, prec)
+    G.mps_set_state(M, st.B, st.lam)
+    dwg = G.mps_apply_gates(M, np.array(bonds, dtype=np.int32), Us)
+    dw = mps.apply_gates(st, list(zip(bonds, Us)), chi)
+    rg, sites, lams = G.mps_get_state(M)
+    assert list(rg) == st.ranks()
+    lam_err = max(np.abs(a - b).max() for a, b in zip(lams, st.lam))
+    rng = np.random.default_rng(8)
+    codes = rng.integers(0, 4, size=(40, n)).astype(np.uint8)
+    vals = G.mps_expect_paulis(M, codes)
+    ref = np.array([mps.expect_string(st, c) for c in codes]) / mps.norm2(st)
+    print(f"brickwork chi128 prec={prec}: lambda err {lam_err:.3e}, max|d<P>| {np.abs(vals - ref).max():.3e}, "
+          f"discarded gpu {dwg:.4e} oracle {dw:.4e}")
+    if prec == G.MPS_FP64:
+        assert lam_err <= 1e-10 and np.abs(vals - ref).max() <= 1e-10 and abs(dwg - dw) <= 1e-12
+    else:
+        assert lam_err <= 1e-5 and np.abs(vals - ref).max() <= 1e-5 and abs(dwg - dw) <= 1e-6
