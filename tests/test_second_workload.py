@@ -48,7 +48,8 @@ def test_mps_inspired_circuit_12q_equals_statevector(prec):
     err = np.abs(got - psi).max()
     print(f"MPS-inspired 12q prec={prec}: max|d psi| = {err:.3e}, discarded {dw:.2e}")
     if prec == G.MPS_FP64:
-        assert err <= 1e-12 and dw < 1e-20
+        # the discarded fraction is (|M'|^2 - kept) / |M'|^2 in FP64: rounding only
+        assert err <= 1e-12 and dw < 1e-11
     else:
         assert err <= 2e-6
 
