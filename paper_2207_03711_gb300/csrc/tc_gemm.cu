@@ -16,7 +16,8 @@
 // FP32 additions; two TMEM buffers alternate so that the MMAs of tile k+1 run while the
 // epilogue reads tile k.
 //
-// One CTA computes one 128 x 128 tile of C with 192 threads:
+// A persistent grid (at most one CTA per SM) walks the 128 x 128 tiles of C; each CTA
+// runs 192 threads:
 //   warp 0, lane 0  TMA producer: four K-major 128-byte-swizzled 128 x 32 tiles per
 //                   stage (A_hi, A_lo, B_hi, B_lo), three stages of 64 KB
 //   warp 1          allocates 256 TMEM columns (two 128-column accumulators); lane 0
@@ -171,8 +172,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* freed = bars + 2 * STAGES + 2;
   uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nk = (K + BK - 1) / BK;
+  const int tiles_n = (N + BN - 1) / BN, tiles = tiles_n * ((M + BM - 1) / BM);
+  // persistent: this CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the
+  // pipeline counters (stage and accumulator phases) run on across its tiles, so the
+  // loads and MMAs of the next tile overlap the epilogue of the previous one
+  const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (tid == 0) {
     for (int s = 0; s < 2 * STAGES + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
@@ -194,24 +199,34 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ---- TMA producer
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmAh)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBh)) : "memory");
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES;
-      if (kt >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((kt / STAGES) & 1) ^ 1, err, 1)) break;
-      unsigned char* st = base + s * STAGE_BYTES;
-      const uint32_t fb = smem_u32(&full[s]);
-      mbar_arrive_expect_tx(fb, STAGE_BYTES);
-      tma_load_2d(smem_u32(st), &tmAh, kt * BK, m0, fb);
-      tma_load_2d(smem_u32(st + TILE_A), &tmAl, kt * BK, m0, fb);
-      tma_load_2d(smem_u32(st + 2 * TILE_A), &tmBh, kt * BK, n0, fb);
-      tma_load_2d(smem_u32(st + 2 * TILE_A + TILE_B), &tmBl, kt * BK, n0, fb);
+    int g = 0;   // K tiles issued by this CTA
+    bool ok = true;
+    for (int n = 0; n < my_tiles && ok; ++n) {
+      const int tile = blockIdx.x + n * gridDim.x;
+      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      for (int kt = 0; kt < nk; ++kt, ++g) {
+        const int s = g % STAGES;
+        if (g >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((g / STAGES) & 1) ^ 1, err, 1)) {
+          ok = false;
+          break;
+        }
+        unsigned char* st = base + s * STAGE_BYTES;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_arrive_expect_tx(fb, STAGE_BYTES);
+        tma_load_2d(smem_u32(st), &tmAh, kt * BK, m0, fb);
+        tma_load_2d(smem_u32(st + TILE_A), &tmAl, kt * BK, m0, fb);
+        tma_load_2d(smem_u32(st + 2 * TILE_A), &tmBh, kt * BK, n0, fb);
+        tma_load_2d(smem_u32(st + 2 * TILE_A + TILE_B), &tmBl, kt * BK, n0, fb);
+      }
     }
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: K tile kt goes to accumulator kt & 1, from zero
+    // ---- MMA issuer: K tile g goes to accumulator g & 1, from zero
     constexpr uint32_t idesc = idesc_tf32(BM, BN);
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES, b = kt & 1;
-      if (!mbar_wait(smem_u32(&full[s]), (kt / STAGES) & 1, err, 2)) break;
-      if (kt >= 2 && !mbar_wait(smem_u32(&freed[b]), ((kt >> 1) & 1) ^ 1, err, 4)) break;
+    const int total = my_tiles * nk;
+    for (int g = 0; g < total; ++g) {
+      const int s = g % STAGES, b = g & 1;
+      if (!mbar_wait(smem_u32(&full[s]), (g / STAGES) & 1, err, 2)) break;
+      if (g >= 2 && !mbar_wait(smem_u32(&freed[b]), ((g >> 1) & 1) ^ 1, err, 4)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = smem_u32(base + s * STAGE_BYTES);
       const uint32_t acc = tmem + (uint32_t)(b * BN);
@@ -227,38 +242,43 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mma_tf32(acc, al, bh, idesc, 1u);
       }
       mma_commit(smem_u32(&empty[s]));   // stage s free once these finish
-      mma_commit(smem_u32(&ready[b]));   // K tile kt complete in accumulator b
+      mma_commit(smem_u32(&ready[b]));   // K tile g complete in accumulator b
     }
   } else if (warp >= 2) {
     // ---- epilogue: round-to-nearest FP32 sums of the K tiles, one row per thread
     const int q = warp & 3;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-    float sum[BN];
-#pragma unroll
-    for (int c = 0; c < BN; ++c) sum[c] = 0.f;
     bool ok = true;
-    for (int kt = 0; kt < nk && ok; ++kt) {
-      const int b = kt & 1;
-      ok = mbar_wait(smem_u32(&ready[b]), (kt >> 1) & 1, err, 3);
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      if (ok) {
+    int g = 0;
+    for (int n = 0; n < my_tiles && ok; ++n) {
+      const int tile = blockIdx.x + n * gridDim.x;
+      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
+      float sum[BN];
 #pragma unroll
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-          float v[32];
-          tmem_ld32(tmem + lane_off + (uint32_t)(b * BN + c0), v);
+      for (int c = 0; c < BN; ++c) sum[c] = 0.f;
+      for (int kt = 0; kt < nk && ok; ++kt, ++g) {
+        const int b = g & 1;
+        ok = mbar_wait(smem_u32(&ready[b]), (g >> 1) & 1, err, 3);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) sum[c0 + j] = __fadd_rn(sum[c0 + j], v[j]);
+          for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            tmem_ld32(tmem + lane_off + (uint32_t)(b * BN + c0), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) sum[c0 + j] = __fadd_rn(sum[c0 + j], v[j]);
+          }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(smem_u32(&freed[b]));
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(smem_u32(&freed[b]));
-    }
-    const int row = m0 + q * 32 + lane;
-    if (ok && row < M) {
-      float* out = C + (size_t)row * ldc + n0;
+      const int row = m0 + q * 32 + lane;
+      if (ok && row < M) {
+        float* out = C + (size_t)row * ldc + n0;
 #pragma unroll
-      for (int c = 0; c < BN; ++c)
-        if (n0 + c < N) out[c] = sum[c];
+        for (int c = 0; c < BN; ++c)
+          if (n0 + c < N) out[c] = sum[c];
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -354,7 +374,12 @@ cudaError_t launch_gemm_tf32x3(const SplitPlane& A, const SplitPlane& B, int M, 
     attr[dev] = cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   });
   if (attr[dev] != cudaSuccess) return attr[dev];
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  // persistent grid: one CTA per SM at most (197 KB of shared memory each)
+  static int sm_count[64] = {0};
+  if (!sm_count[dev] && (e = cudaDeviceGetAttribute(&sm_count[dev], cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  const int grid = (int)std::min<int64_t>(tiles, sm_count[dev]);
   k_gemm_tf32x3<<<grid, NTHREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, C, ldc, M, N, K, err);
   return cudaGetLastError();
 }
