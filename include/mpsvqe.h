@@ -121,7 +121,7 @@ int circ_destroy(circ_t circ);
  * current device, each initialised to the all-zero product state. precision:
  * MPS_FP64 (complex128 tensors, FP64 SVD and contractions) or MPS_MIXED (complex64
  * tensors, FP32 SVD with a compensated re-orthonormalisation of the kept singular
- * vectors, FP32 gate contractions, environment contractions of bonds >= 32 on the
+ * vectors, FP32 gate contractions, environment contractions of bonds >= 128 on the
  * tensor cores with compensated TF32 splits, FP64 Schmidt numbers and energy sums).
  * cuda_stream: a cudaStream_t (NULL = default stream). Device memory is taken and
  * returned stream-ordered on that stream. n_qubits in [2, 128], chi in [1, 256],
