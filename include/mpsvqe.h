@@ -296,13 +296,15 @@ int mps_apply_gates_noalloc(int n_qubits, int chi, void* site_tensors, const int
 
 /* Real GEMM on the tensor cores (tcgen05, TMEM, TMA) with compensated TF32 splits:
  * C = A . B^T with A (M x K), B (N x K), C (M x N), all FP32 row-major DEVICE arrays
- * with leading dimensions lda, ldb >= K and ldc >= N. Each operand is split into
- * hi = tf32(x) and lo = tf32(x - hi) and C is accumulated in FP32 as
- * A_hi B_hi + A_hi B_lo + A_lo B_hi (relative error about 2^-21 of sum |a||b|). This
- * is the contraction primitive of the environment sweeps (Eq. 11, Sec. III-C) in
- * mixed precision, exported for tests and callers with their own operands. Takes
- * temporary device memory for the split planes with cudaMallocAsync on cuda_stream and
- * waits for the stream. Returns MPS_EINVAL for bad sizes or null pointers, MPS_ENOMEM,
+ * with leading dimensions lda, ldb >= K and ldc >= N. Inside the kernel each loaded
+ * tile is split into hi = tf32(x) and lo = tf32(x - hi) and C is accumulated as
+ * A_hi B_hi + A_hi B_lo + A_lo B_hi, each 32-wide K slice from zero, the slices summed
+ * in round-to-nearest FP32 (relative error about 2^-21 of sum |a||b|, no drift with K).
+ * This is the contraction primitive of the environment sweeps (Eq. 11, Sec. III-C) in
+ * mixed precision, exported for tests and callers with their own operands. Takes a
+ * small temporary error word, and a padded copy of any operand whose rows do not start
+ * on 16-byte boundaries (lda or ldb not a multiple of 4, or a misaligned pointer), with
+ * cudaMallocAsync on cuda_stream, and waits for the stream. Returns MPS_EINVAL for bad sizes or null pointers, MPS_ENOMEM,
  * MPS_ECUDA, or MPS_ETIMEOUT if a bounded pipeline wait inside the kernel ran out. */
 int mps_tc_gemm_tf32x3(int M, int N, int K, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
                        int64_t ldc, void* cuda_stream);

@@ -13,8 +13,9 @@
 //   GEMM-C: AC (4D' x 2D) times rows (u, j, c) of [Re T_j[u][:, c] | Im T_j[u][:, c]]^T
 //           AC row (i, re, c') = [ Re B^i[:, c'],  Im B^i[:, c'] ],
 //           AC row (i, im, c') = [-Im B^i[:, c'],  Re B^i[:, c'] ]
-// Both run on tc::launch_gemm_tf32x3 (tcgen05, compensated TF32 splits). The kernels
-// here build the split operand planes and move results between the GEMM layouts and
+// Both run on tc::launch_gemm_tf32x3 (tcgen05, compensated TF32 splits made inside the
+// GEMM from the FP32 tiles it loads). The kernels here build the FP32 operand planes and
+// move results between the GEMM layouts and
 // the complex environment buffers that the rest of the measurement uses (L: node u at
 // u chi^2, leading dimension D; T: T_j[u] at (2u + j) chi^2, leading dimension D').
 #include <cstdint>
@@ -25,19 +26,11 @@
 
 namespace mpsvqe {
 
-__device__ __forceinline__ void split_tf32(float v, float& h, float& l) {
-  uint32_t hb, lb;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
-  h = __uint_as_float(hb);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(v - h));
-  l = __uint_as_float(lb);
-}
-
 __host__ __device__ inline int64_t round4(int64_t x) { return (x + 3) & ~(int64_t)3; }
 
 // ---------------------------------------------------------------- operand planes
 // [Re L[u][a][:] | Im L[u][a][:]] for rows (u, a), leading dimension ldk.
-__global__ void k_tc_split_L(const Cx<float>* L, int64_t chi2, int U, int D, float* h, float* l, int64_t ldk) {
+__global__ void k_tc_pack_L(const Cx<float>* L, int64_t chi2, int U, int D, float* out, int64_t ldk) {
   const int64_t total = (int64_t)U * D * ldk;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = i / ldk, col = i - row * ldk;
@@ -47,13 +40,12 @@ __global__ void k_tc_split_L(const Cx<float>* L, int64_t chi2, int U, int D, flo
       const Cx<float> z = L[(size_t)u * chi2 + (size_t)a * D + (col < D ? col : col - D)];
       v = col < D ? z.x : z.y;
     }
-    split_tf32(v, h[i], l[i]);
+    out[i] = v;
   }
 }
 
 // BT (4D' x ldk) and AC (4D' x ldk) from site k (B[b][j][c] at (b 2 + j) D' + c).
-__global__ void k_tc_site_operands(const Cx<float>* Bk, int D, int Dp, int64_t ldk, float* bth, float* btl,
-                                   float* ach, float* acl) {
+__global__ void k_tc_site_operands(const Cx<float>* Bk, int D, int Dp, int64_t ldk, float* bt, float* ac) {
   const int64_t total = (int64_t)4 * Dp * ldk;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = i / ldk;
@@ -68,8 +60,8 @@ __global__ void k_tc_site_operands(const Cx<float>* Bk, int D, int Dp, int64_t l
       // AC: re row [Br, Bi], im row [-Bi, Br]
       va = ro == 0 ? (ri == 0 ? z.x : z.y) : (ri == 0 ? -z.y : z.x);
     }
-    split_tf32(vt, bth[i], btl[i]);
-    split_tf32(va, ach[i], acl[i]);
+    bt[i] = vt;
+    ac[i] = va;
   }
 }
 
@@ -90,8 +82,7 @@ __global__ void k_tc_scatter_T(const float* CT, int U, int D, int Dp, Cx<float>*
 
 // Rows (u - pa, j, c) of [Re T_j[u][:, c] | Im T_j[u][:, c]] for parents u in [pa, pb):
 // a transpose of each D x D' block through 32 x 32 shared-memory tiles.
-__global__ void k_tc_split_TT(const Cx<float>* T, int64_t chi2, int pa, int D, int Dp, float* h, float* l,
-                              int64_t ldk) {
+__global__ void k_tc_pack_TT(const Cx<float>* T, int64_t chi2, int pa, int D, int Dp, float* out, int64_t ldk) {
   __shared__ Cx<float> tile[32][33];
   const int blk = blockIdx.z;               // (u - pa) * 2 + j
   const int u = pa + (blk >> 1), j = blk & 1;
@@ -107,8 +98,8 @@ __global__ void k_tc_split_TT(const Cx<float>* T, int64_t chi2, int pa, int D, i
     if (c < Dp && a < D) {
       const Cx<float> z = tile[threadIdx.x][y];
       const int64_t row = ((int64_t)blk * Dp + c) * ldk;
-      split_tf32(z.x, h[row + a], l[row + a]);
-      split_tf32(z.y, h[row + D + a], l[row + D + a]);
+      out[row + a] = z.x;
+      out[row + D + a] = z.y;
     }
   }
   // zero padding columns 2D..ldk-1 of the rows this block owns (first a-tile only)
@@ -118,8 +109,7 @@ __global__ void k_tc_split_TT(const Cx<float>* T, int64_t chi2, int pa, int D, i
       if (c < Dp)
         for (int col = 2 * D + threadIdx.x; col < ldk; col += 32) {
           const int64_t row = ((int64_t)blk * Dp + c) * ldk;
-          h[row + col] = 0.f;
-          l[row + col] = 0.f;
+          out[row + col] = 0.f;
         }
     }
   }
@@ -165,18 +155,18 @@ static inline int grid_for(int64_t total) {
 
 size_t env_tc_scratch_floats(int chi, int max_nodes) {
   const int64_t D = chi, Dp = chi, U = max_nodes, ldk = round4(2 * D);
-  const int64_t lplanes = 2 * U * D * ldk;          // L hi/lo
-  const int64_t site = 4 * 4 * Dp * ldk;            // BT hi/lo, AC hi/lo
+  const int64_t lplane = U * D * ldk;               // [Re L | Im L]
+  const int64_t site = 2 * 4 * Dp * ldk;            // BT, AC
   const int64_t ct = U * D * 4 * Dp;                // GEMM-T output
-  const int64_t tt = 2 * U * 2 * Dp * ldk;          // TT hi/lo
+  const int64_t tt = U * 2 * Dp * ldk;              // [Re T^T | Im T^T]
   const int64_t cl = 4 * Dp * U * 2 * Dp;           // GEMM-C output
   const int64_t pad = 64;                           // 16-byte alignment of each part
-  return (size_t)(lplanes + site + ct + tt + cl + 16 * pad);
+  return (size_t)(lplane + site + ct + tt + cl + 8 * pad);
 }
 
 namespace {
 struct Parts {
-  float *lh, *ll, *bth, *btl, *ach, *acl, *ct, *tth, *ttl, *cl;
+  float *lp, *bt, *ac, *ct, *tt, *cl;
 };
 Parts carve(float* base, int chi, int max_nodes) {
   const int64_t D = chi, Dp = chi, U = max_nodes, ldk = round4(2 * D);
@@ -186,15 +176,11 @@ Parts carve(float* base, int chi, int max_nodes) {
     return p;
   };
   Parts p;
-  p.lh = take(U * D * ldk);
-  p.ll = take(U * D * ldk);
-  p.bth = take(4 * Dp * ldk);
-  p.btl = take(4 * Dp * ldk);
-  p.ach = take(4 * Dp * ldk);
-  p.acl = take(4 * Dp * ldk);
+  p.lp = take(U * D * ldk);
+  p.bt = take(4 * Dp * ldk);
+  p.ac = take(4 * Dp * ldk);
   p.ct = take(U * D * 4 * Dp);
-  p.tth = take(U * 2 * Dp * ldk);
-  p.ttl = take(U * 2 * Dp * ldk);
+  p.tt = take(U * 2 * Dp * ldk);
   p.cl = take(4 * Dp * U * 2 * Dp);
   return p;
 }
@@ -203,7 +189,7 @@ Parts carve(float* base, int chi, int max_nodes) {
 cudaError_t env_tc_site(const EnvTc& s, const Cx<float>* Bk, int D, int Dp, cudaStream_t st) {
   const Parts p = carve(s.scratch, s.chi, s.max_nodes);
   const int64_t ldk = round4(2 * D);
-  k_tc_site_operands<<<grid_for(4 * Dp * ldk), 256, 0, st>>>(Bk, D, Dp, ldk, p.bth, p.btl, p.ach, p.acl);
+  k_tc_site_operands<<<grid_for(4 * Dp * ldk), 256, 0, st>>>(Bk, D, Dp, ldk, p.bt, p.ac);
   return cudaGetLastError();
 }
 
@@ -212,12 +198,12 @@ cudaError_t env_tc_T(const EnvTc& s, const Cx<float>* L, Cx<float>* T, int U, in
   if (U <= 0) return cudaSuccess;
   const Parts p = carve(s.scratch, s.chi, s.max_nodes);
   const int64_t ldk = round4(2 * D), chi2 = (int64_t)s.chi * s.chi;
-  k_tc_split_L<<<grid_for((int64_t)U * D * ldk), 256, 0, st>>>(L, chi2, U, D, p.lh, p.ll, ldk);
+  k_tc_pack_L<<<grid_for((int64_t)U * D * ldk), 256, 0, st>>>(L, chi2, U, D, p.lp, ldk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (e0 && (e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
-  e = tc::launch_gemm_tf32x3(tc::SplitPlane{p.lh, p.ll, ldk}, tc::SplitPlane{p.bth, p.btl, ldk}, U * D, 4 * Dp,
-                             2 * D, p.ct, 4 * Dp, s.err, st);
+  e = tc::launch_gemm_tf32x3(tc::Plane{p.lp, ldk}, tc::Plane{p.bt, ldk}, U * D, 4 * Dp, 2 * D, p.ct, 4 * Dp, s.err,
+                             st);
   if (e != cudaSuccess) return e;
   if (e1 && (e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
   k_tc_scatter_T<<<grid_for((int64_t)U * 2 * D * Dp), 256, 0, st>>>(p.ct, U, D, Dp, T, chi2);
@@ -231,14 +217,12 @@ cudaError_t env_tc_children(const EnvTc& s, const Cx<float>* T, int pa, int pb, 
   const Parts p = carve(s.scratch, s.chi, s.max_nodes);
   const int64_t ldk = round4(2 * D), chi2 = (int64_t)s.chi * s.chi;
   const int np = pb - pa;
-  k_tc_split_TT<<<dim3((Dp + 31) / 32, (D + 31) / 32, np * 2), dim3(32, 8), 0, st>>>(T, chi2, pa, D, Dp, p.tth, p.ttl,
-                                                                                     ldk);
+  k_tc_pack_TT<<<dim3((Dp + 31) / 32, (D + 31) / 32, np * 2), dim3(32, 8), 0, st>>>(T, chi2, pa, D, Dp, p.tt, ldk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t N = (int64_t)np * 2 * Dp;
   if (e0 && (e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
-  e = tc::launch_gemm_tf32x3(tc::SplitPlane{p.ach, p.acl, ldk}, tc::SplitPlane{p.tth, p.ttl, ldk}, 4 * Dp, (int)N,
-                             2 * D, p.cl, N, s.err, st);
+  e = tc::launch_gemm_tf32x3(tc::Plane{p.ac, ldk}, tc::Plane{p.tt, ldk}, 4 * Dp, (int)N, 2 * D, p.cl, N, s.err, st);
   if (e != cudaSuccess) return e;
   if (e1 && (e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
   k_tc_combine<<<grid_for((int64_t)nc * Dp * Dp), 256, 0, st>>>(p.cl, N, Dp, parent, edge, nc, node_base, pa, Lout,

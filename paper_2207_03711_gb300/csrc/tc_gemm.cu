@@ -1,11 +1,12 @@
 // Real GEMM on the fifth-generation tensor cores of sm_103a (tcgen05 + TMEM + TMA)
 // with compensated TF32 splits, the contraction primitive of the environment sweeps.
 //
-// C (M x N, FP32) = A (M x K) . B (N x K)^T, both operands K-major (row-major with K
-// contiguous). Each operand is given as two FP32 planes, hi = tf32(x) and
-// lo = tf32(x - hi); the product is accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi,
+// C (M x N, FP32) = A (M x K) . B (N x K)^T, both FP32 operands K-major (row-major with K
+// contiguous). Inside the kernel every loaded tile is split into hi = tf32(x) and
+// lo = tf32(x - hi), and the product is accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi,
 // which recovers the bits a single TF32 product drops (relative error ~2^-21 instead of
-// ~2^-11).
+// ~2^-11). Splitting after the load keeps the traffic from L2 at one FP32 plane per
+// operand.
 //
 // The tensor core's FP32 accumulation rounds toward zero: measured on a GB300 with
 // positive operands, the mean relative error grows linearly with K (-5e-6 at K = 512,
@@ -17,18 +18,23 @@
 // epilogue reads tile k.
 //
 // A persistent grid (at most one CTA per SM) walks the 128 x 128 tiles of C; each CTA
-// runs 192 threads:
-//   warp 0, lane 0  TMA producer: four K-major 128-byte-swizzled 128 x 32 tiles per
-//                   stage (A_hi, A_lo, B_hi, B_lo), three stages of 64 KB
+// runs 448 threads:
+//   warp 0, lane 0  TMA producer: K-major 128-byte-swizzled 128 x 32 FP32 tiles of A and
+//                   B per stage, three stages
 //   warp 1          allocates 256 TMEM columns (two 128-column accumulators); lane 0
 //                   issues tcgen05.mma (M 128, N 128, K 8) three times per K step,
 //                   frees each stage back to the producer and hands each finished
 //                   K tile to the epilogue through mbarriers
-//   warps 2..5      epilogue: tcgen05.ld of the tile (warp w reads TMEM lanes
-//                   32 (w mod 4) ..), FP32 running sums in registers, bounds-checked
-//                   stores of C
-// Every mbarrier wait is bounded: a wait that runs out records an error code in
-// *err, and the kernel still passes its final barrier, frees its TMEM and returns.
+//   warps 2..9      epilogue: tcgen05.ld of the tile (warp w reads TMEM lanes
+//                   32 (w mod 4) .. and half of the 128 columns), FP32 running sums in
+//                   registers, bounds-checked stores of C
+//   warps 10..13    split each loaded stage in shared memory: hi over the loaded tile,
+//                   lo beside it (same swizzled offsets), then a proxy fence so the
+//                   tensor core sees the stores
+// The pipeline counters run on across a CTA's tiles, so the loads and MMAs of the next
+// tile overlap the epilogue of the previous one. Every mbarrier wait is bounded: a wait
+// that runs out records an error code in *err, and the kernel still passes its final
+// barrier, frees its TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -49,10 +55,13 @@ constexpr int STAGES = 3;
 constexpr int TILE_A = BM * BK * 4;                   // 16 KB
 constexpr int TILE_B = BN * BK * 4;                   // 16 KB
 constexpr int STAGE_BYTES = 2 * TILE_A + 2 * TILE_B;  // hi and lo of both operands: 64 KB
-constexpr int NBARS = 2 * STAGES + 4;                 // full, empty per stage; tile ready, tile free per buffer
+constexpr int NBARS = 3 * STAGES + 4;                 // full, split, empty per stage; ready, free per buffer
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 8 * NBARS + 16;
-constexpr int NTHREADS = 192;
-constexpr int NEPI = 128;                             // epilogue threads (warps 2..5)
+constexpr int NTHREADS = 448;
+constexpr int NEPI = 256;                             // epilogue threads (warps 2..9)
+constexpr int EPI_COLS = BN / 2;                      // columns per epilogue thread
+constexpr int CONV_WARP0 = 10;                        // split threads (warps 10..13)
+constexpr int NCONV = 128;
 constexpr int TMEM_COLS = 2 * BN;                     // two accumulators
 constexpr long long kWaitCycles = 4000000000LL;       // ~2 s at 2 GHz
 
@@ -158,29 +167,35 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ float tf32_rna(float v) {
+  uint32_t b;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(b) : "f"(v));
+  return __uint_as_float(b);
+}
+
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, float* C,
+    k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float* C,
                   int64_t ldc, int M, int N, int K, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  // barriers: full[s], empty[s] (s < STAGES), ready[b], freed[b] (b < 2)
+  // barriers: full[s] (TMA), split[s] (hi/lo written), empty[s] (MMAs done), ready[b], freed[b]
   uint64_t* bars = (uint64_t*)(base + STAGES * STAGE_BYTES);
   uint64_t* full = bars;
-  uint64_t* empty = bars + STAGES;
-  uint64_t* ready = bars + 2 * STAGES;
-  uint64_t* freed = bars + 2 * STAGES + 2;
+  uint64_t* split = bars + STAGES;
+  uint64_t* empty = bars + 2 * STAGES;
+  uint64_t* ready = bars + 3 * STAGES;
+  uint64_t* freed = bars + 3 * STAGES + 2;
   uint32_t* tmem_slot = (uint32_t*)(bars + NBARS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nk = (K + BK - 1) / BK;
   const int tiles_n = (N + BN - 1) / BN, tiles = tiles_n * ((M + BM - 1) / BM);
   // persistent: this CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; the
-  // pipeline counters (stage and accumulator phases) run on across its tiles, so the
-  // loads and MMAs of the next tile overlap the epilogue of the previous one
+  // pipeline counters (stage and accumulator phases) run on across its tiles
   const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int total = my_tiles * nk;
 
   if (tid == 0) {
-    for (int s = 0; s < 2 * STAGES + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < 3 * STAGES + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
     for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&freed[b]), NEPI);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -196,10 +211,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmAh)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmBh)) : "memory");
-    int g = 0;   // K tiles issued by this CTA
+    // ---- TMA producer: the FP32 tiles of A and B, into the hi slots of the stage
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    int g = 0;
     bool ok = true;
     for (int n = 0; n < my_tiles && ok; ++n) {
       const int tile = blockIdx.x + n * gridDim.x;
@@ -212,20 +227,72 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         unsigned char* st = base + s * STAGE_BYTES;
         const uint32_t fb = smem_u32(&full[s]);
-        mbar_arrive_expect_tx(fb, STAGE_BYTES);
-        tma_load_2d(smem_u32(st), &tmAh, kt * BK, m0, fb);
-        tma_load_2d(smem_u32(st + TILE_A), &tmAl, kt * BK, m0, fb);
-        tma_load_2d(smem_u32(st + 2 * TILE_A), &tmBh, kt * BK, n0, fb);
-        tma_load_2d(smem_u32(st + 2 * TILE_A + TILE_B), &tmBl, kt * BK, n0, fb);
+        mbar_arrive_expect_tx(fb, TILE_A + TILE_B);
+        tma_load_2d(smem_u32(st), &tmA, kt * BK, m0, fb);
+        tma_load_2d(smem_u32(st + 2 * TILE_A), &tmB, kt * BK, n0, fb);
       }
+    }
+    // no copy may still be landing in shared memory when the CTA exits: wait (bounded)
+    // for the last load of each stage (already complete unless a consumer gave up)
+    for (int gl = g - 1; gl >= 0 && gl >= g - STAGES; --gl)
+      mbar_wait(smem_u32(&full[gl % STAGES]), (gl / STAGES) & 1, err, 6);
+  } else if (warp >= CONV_WARP0) {
+    // ---- split: hi = tf32(x) over the loaded tile, lo = tf32(x - hi) beside it
+    const int ct = tid - CONV_WARP0 * 32;
+    for (int g = 0; g < total; ++g) {
+      const int s = g % STAGES;
+      const bool got = mbar_wait(smem_u32(&full[s]), (g / STAGES) & 1, err, 5);
+      // all split threads leave together if any wait ran out (none is left at a barrier)
+      uint32_t all_ok;
+      asm volatile(
+          "{\n"
+          " .reg .pred p, q;\n"
+          " setp.ne.u32 p, %1, 0;\n"
+          " bar.red.and.pred q, 1, %2, p;\n"
+          " selp.u32 %0, 1, 0, q;\n"
+          "}\n"
+          : "=r"(all_ok)
+          : "r"((uint32_t)got), "n"(NCONV)
+          : "memory");
+      if (!all_ok) break;
+      unsigned char* st = base + s * STAGE_BYTES;
+      float4* ah = (float4*)st;
+      float4* al = (float4*)(st + TILE_A);
+      float4* bh = (float4*)(st + 2 * TILE_A);
+      float4* bl = (float4*)(st + 2 * TILE_A + TILE_B);
+#pragma unroll 4
+      for (int v = ct; v < TILE_A / 16; v += NCONV) {
+        const float4 x = ah[v];
+        float4 h, l;
+        h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
+        h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
+        h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
+        h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
+        ah[v] = h;
+        al[v] = l;
+      }
+#pragma unroll 4
+      for (int v = ct; v < TILE_B / 16; v += NCONV) {
+        const float4 x = bh[v];
+        float4 h, l;
+        h.x = tf32_rna(x.x); l.x = tf32_rna(x.x - h.x);
+        h.y = tf32_rna(x.y); l.y = tf32_rna(x.y - h.y);
+        h.z = tf32_rna(x.z); l.z = tf32_rna(x.z - h.z);
+        h.w = tf32_rna(x.w); l.w = tf32_rna(x.w - h.w);
+        bh[v] = h;
+        bl[v] = l;
+      }
+      // the generic-proxy stores must be visible to the tensor core (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("bar.sync 2, %0;" ::"n"(NCONV) : "memory");
+      if (ct == 0) mbar_arrive(smem_u32(&split[s]));
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: K tile g goes to accumulator g & 1, from zero
     constexpr uint32_t idesc = idesc_tf32(BM, BN);
-    const int total = my_tiles * nk;
     for (int g = 0; g < total; ++g) {
       const int s = g % STAGES, b = g & 1;
-      if (!mbar_wait(smem_u32(&full[s]), (g / STAGES) & 1, err, 2)) break;
+      if (!mbar_wait(smem_u32(&split[s]), (g / STAGES) & 1, err, 2)) break;
       if (g >= 2 && !mbar_wait(smem_u32(&freed[b]), ((g >> 1) & 1) ^ 1, err, 4)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t st = smem_u32(base + s * STAGE_BYTES);
@@ -245,26 +312,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mma_commit(smem_u32(&ready[b]));   // K tile g complete in accumulator b
     }
   } else if (warp >= 2) {
-    // ---- epilogue: round-to-nearest FP32 sums of the K tiles, one row per thread
-    const int q = warp & 3;
+    // ---- epilogue: round-to-nearest FP32 sums of the K tiles; warp w reads TMEM lanes
+    // 32 (w mod 4) .. (its rows) and one half of the columns
+    const int q = warp & 3, c_lo = ((warp - 2) >> 2) * EPI_COLS;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const bool vec = ((ldc & 3) == 0) && (((uintptr_t)C & 15) == 0);
     bool ok = true;
     int g = 0;
     for (int n = 0; n < my_tiles && ok; ++n) {
       const int tile = blockIdx.x + n * gridDim.x;
-      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN;
-      float sum[BN];
+      const int m0 = (tile / tiles_n) * BM, n0 = (tile % tiles_n) * BN + c_lo;
+      float sum[EPI_COLS];
 #pragma unroll
-      for (int c = 0; c < BN; ++c) sum[c] = 0.f;
+      for (int c = 0; c < EPI_COLS; ++c) sum[c] = 0.f;
       for (int kt = 0; kt < nk && ok; ++kt, ++g) {
         const int b = g & 1;
-        ok = mbar_wait(smem_u32(&ready[b]), (g >> 1) & 1, err, 3);
+        // tcgen05.ld is warp-collective: the whole warp goes on or stops together
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ready[b]), (g >> 1) & 1, err, 3));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (ok) {
 #pragma unroll
-          for (int c0 = 0; c0 < BN; c0 += 32) {
+          for (int c0 = 0; c0 < EPI_COLS; c0 += 32) {
             float v[32];
-            tmem_ld32(tmem + lane_off + (uint32_t)(b * BN + c0), v);
+            tmem_ld32(tmem + lane_off + (uint32_t)(b * BN + c_lo + c0), v);
 #pragma unroll
             for (int j = 0; j < 32; ++j) sum[c0 + j] = __fadd_rn(sum[c0 + j], v[j]);
           }
@@ -275,9 +345,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int row = m0 + q * 32 + lane;
       if (ok && row < M) {
         float* out = C + (size_t)row * ldc + n0;
+        if (vec && n0 + EPI_COLS <= N) {
 #pragma unroll
-        for (int c = 0; c < BN; ++c)
-          if (n0 + c < N) out[c] = sum[c];
+          for (int c = 0; c < EPI_COLS; c += 4)
+            *reinterpret_cast<float4*>(out + c) = make_float4(sum[c], sum[c + 1], sum[c + 2], sum[c + 3]);
+        } else {
+#pragma unroll
+          for (int c = 0; c < EPI_COLS; ++c)
+            if (n0 + c < N) out[c] = sum[c];
+        }
       }
     }
   }
@@ -289,25 +365,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-// hi = tf32(x) (round to nearest, low 13 mantissa bits zero) and lo = tf32(x - hi) of an
-// M x K row-major plane (leading dimension ld_in) into two planes of leading dimension
-// ld_out (a multiple of 4 floats, so TMA rows start on 16-byte boundaries); columns
-// K..ld_out-1 are written as zero.
-__global__ void k_split_tf32(const float* x, int64_t ld_in, int M, int K, float* hi, float* lo, int64_t ld_out) {
+// Copy of an M x K row-major plane (leading dimension ld_in) into one of leading
+// dimension ld_out (a multiple of 4 floats, so TMA rows start on 16-byte boundaries);
+// columns K..ld_out-1 are written as zero.
+__global__ void k_pad_rows(const float* x, int64_t ld_in, int M, int K, float* out, int64_t ld_out) {
   const int64_t total = (int64_t)M * ld_out;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / ld_out, c = i - r * ld_out;
-    float h = 0.f, l = 0.f;
-    if (c < K) {
-      const float v = x[r * ld_in + c];
-      uint32_t hb, lb;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
-      h = __uint_as_float(hb);
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"(v - h));
-      l = __uint_as_float(lb);
-    }
-    hi[i] = h;
-    lo[i] = l;
+    out[i] = c < K ? x[r * ld_in + c] : 0.f;
   }
 }
 
@@ -344,27 +409,23 @@ static cudaError_t make_map(CUtensorMap* map, const float* p, int rows, int K, i
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_split_tf32(const float* x, int64_t ld_in, int M, int K, float* hi, float* lo, int64_t ld_out,
-                              cudaStream_t st) {
+cudaError_t launch_pad_rows(const float* x, int64_t ld_in, int M, int K, float* out, int64_t ld_out,
+                            cudaStream_t st) {
   if (M <= 0 || ld_out <= 0) return cudaSuccess;
   const int64_t total = (int64_t)M * ld_out;
   const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-  k_split_tf32<<<blocks, 256, 0, st>>>(x, ld_in, M, K, hi, lo, ld_out);
+  k_pad_rows<<<blocks, 256, 0, st>>>(x, ld_in, M, K, out, ld_out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_tf32x3(const SplitPlane& A, const SplitPlane& B, int M, int N, int K, float* C, int64_t ldc,
-                               int* err, cudaStream_t st) {
+cudaError_t launch_gemm_tf32x3(const Plane& A, const Plane& B, int M, int N, int K, float* C, int64_t ldc, int* err,
+                               cudaStream_t st) {
   if (M <= 0 || N <= 0) return cudaSuccess;
-  if ((A.ld & 3) || (B.ld & 3) || ((uintptr_t)A.hi & 15) || ((uintptr_t)A.lo & 15) || ((uintptr_t)B.hi & 15) ||
-      ((uintptr_t)B.lo & 15))
-    return cudaErrorInvalidValue;
-  CUtensorMap ah, al, bh, bl;
+  if ((A.ld & 3) || (B.ld & 3) || ((uintptr_t)A.p & 15) || ((uintptr_t)B.p & 15)) return cudaErrorInvalidValue;
+  CUtensorMap am, bm;
   cudaError_t e;
-  if ((e = make_map(&ah, A.hi, M, K, A.ld, BM)) != cudaSuccess) return e;
-  if ((e = make_map(&al, A.lo, M, K, A.ld, BM)) != cudaSuccess) return e;
-  if ((e = make_map(&bh, B.hi, N, K, B.ld, BN)) != cudaSuccess) return e;
-  if ((e = make_map(&bl, B.lo, N, K, B.ld, BN)) != cudaSuccess) return e;
+  if ((e = make_map(&am, A.p, M, K, A.ld, BM)) != cudaSuccess) return e;
+  if ((e = make_map(&bm, B.p, N, K, B.ld, BN)) != cudaSuccess) return e;
   static std::once_flag once[64];
   static cudaError_t attr[64];
   int dev = 0;
@@ -380,7 +441,7 @@ cudaError_t launch_gemm_tf32x3(const SplitPlane& A, const SplitPlane& B, int M, 
     return e;
   const int64_t tiles = (int64_t)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
   const int grid = (int)std::min<int64_t>(tiles, sm_count[dev]);
-  k_gemm_tf32x3<<<grid, NTHREADS, SMEM_BYTES, st>>>(ah, al, bh, bl, C, ldc, M, N, K, err);
+  k_gemm_tf32x3<<<grid, NTHREADS, SMEM_BYTES, st>>>(am, bm, C, ldc, M, N, K, err);
   return cudaGetLastError();
 }
 
@@ -399,23 +460,25 @@ extern "C" int mps_tc_gemm_tf32x3(int M, int N, int K, const float* A, int64_t l
   }
   if (M == 0 || N == 0) return MPS_OK;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // TMA wants 16-byte-aligned rows: operands that are not get a padded copy
+  const bool pad_a = (lda & 3) || ((uintptr_t)A & 15), pad_b = (ldb & 3) || ((uintptr_t)B & 15);
   const int64_t ldk = ((int64_t)K + 3) & ~(int64_t)3;
   float* buf = nullptr;
   int* err = nullptr;
-  const size_t na = (size_t)M * ldk, nb = (size_t)N * ldk;
-  if (cudaMallocAsync((void**)&buf, (2 * na + 2 * nb) * sizeof(float), st) != cudaSuccess ||
+  const size_t na = pad_a ? (size_t)M * ldk : 0, nb = pad_b ? (size_t)N * ldk : 0;
+  if (cudaMallocAsync((void**)&buf, (na + nb + 4) * sizeof(float), st) != cudaSuccess ||
       cudaMallocAsync((void**)&err, sizeof(int), st) != cudaSuccess) {
-    set_error_message("mps_tc_gemm_tf32x3: cudaMallocAsync of the split planes failed");
+    set_error_message("mps_tc_gemm_tf32x3: cudaMallocAsync of the work buffers failed");
     return MPS_ENOMEM;
   }
   int rc = MPS_OK;
   int herr = 0;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), st);
-  if (e == cudaSuccess) e = tc::launch_split_tf32(A, lda, M, K, buf, buf + na, ldk, st);
-  if (e == cudaSuccess) e = tc::launch_split_tf32(B, ldb, N, K, buf + 2 * na, buf + 2 * na + nb, ldk, st);
+  if (e == cudaSuccess && pad_a) e = tc::launch_pad_rows(A, lda, M, K, buf, ldk, st);
+  if (e == cudaSuccess && pad_b) e = tc::launch_pad_rows(B, ldb, N, K, buf + na, ldk, st);
   if (e == cudaSuccess)
-    e = tc::launch_gemm_tf32x3(tc::SplitPlane{buf, buf + na, ldk}, tc::SplitPlane{buf + 2 * na, buf + 2 * na + nb, ldk},
-                               M, N, K, C, ldc, err, st);
+    e = tc::launch_gemm_tf32x3(pad_a ? tc::Plane{buf, ldk} : tc::Plane{A, lda},
+                               pad_b ? tc::Plane{buf + na, ldk} : tc::Plane{B, ldb}, M, N, K, C, ldc, err, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaFreeAsync(buf, st);
   cudaFreeAsync(err, st);

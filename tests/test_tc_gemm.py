@@ -3,9 +3,10 @@ product computed on the host.
 
 The environment sweeps of the measurement (Eq. 11 generalised to Pauli strings,
 Sec. III-C) are dense complex contractions; in mixed precision they run on this
-primitive as real GEMMs. Shapes cover one and several 128 x 256 tiles, ragged edges in
+primitive as real GEMMs. Shapes cover one and several 128 x 128 tiles, ragged edges in
 every dimension, K that is not a multiple of the 32-wide K tile, and leading
-dimensions larger than the logical width. The bound is elementwise,
+dimensions larger than the logical width (padded copies for rows that do not start on
+16-byte boundaries, vector and scalar stores of C). The bound is elementwise,
 |C - AB^T| <= 1e-5 (|A||B|^T): a single TF32 product (10-bit mantissa) misses it by
 about 50x, so the low-order split products are really applied. With one-signed
 operands the mean error must not grow with K (no accumulation bias).
@@ -75,6 +76,24 @@ def test_tc_gemm_has_no_accumulation_bias(K):
     print(f"K={K}: mean relative error {rel.mean():+.2e}, max {np.abs(rel).max():.2e}")
     assert abs(rel.mean()) <= 1e-6
     assert np.abs(rel).max() <= 2e-6
+
+
+def test_tc_gemm_unaligned_operands():
+    """Operands whose rows do not start on 16-byte boundaries (a pointer 4 bytes past an
+    aligned one, leading dimension a multiple of 4) go through a padded copy: the result
+    is the same product."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    M, N, K = 200, 300, 64
+    A = rng.normal(size=(M * K + 1,)).astype(np.float32)
+    B = rng.normal(size=(N * K + 1,)).astype(np.float32)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    dC = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    G.mps_tc_gemm_tf32x3(M, N, K, dA.data_ptr() + 4, K, dB.data_ptr() + 4, K, dC.data_ptr(), N)
+    a = A[1:].reshape(M, K).astype(np.float64)
+    b = B[1:].reshape(N, K).astype(np.float64)
+    err = np.abs(dC.cpu().numpy() - a @ b.T)
+    assert np.all(err <= 1e-5 * (np.abs(a) @ np.abs(b).T))
 
 
 def test_tc_gemm_rejects_bad_sizes():
