@@ -59,8 +59,13 @@ def parse():
     ap.add_argument("--config4-tc-case", action="store_true",
                     help="small profiling case of the tensor-core GEMM: one 64-qubit chi=256 measurement of "
                          "the first --case-strings strings")
+    ap.add_argument("--config3", action="store_true",
+                    help="256 parameter-shift circuits of a 32-qubit chi=128 ansatz per step (one gradient)")
     ap.add_argument("--random-gates", action="store_true",
                     help="second workload: random two-site gates in brickwork order on a random chi=128 MPS")
+    ap.add_argument("--circuit", default="canonical", choices=["canonical", "cancel-ladders"],
+                    help="gate list of the headline workload: the canonical compile, or the circuit-level "
+                         "variant with the CNOT ladders of consecutive commuting rotations cancelled")
     ap.add_argument("--case-strings", type=int, default=2000)
     ap.add_argument("--case-budget-mb", type=int, default=0,
                     help="measurement buffer budget of the tensor-core case (0: the library default)")
@@ -241,11 +246,12 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
-def accuracy_probe(G):
+def accuracy_probe(G, cancel_ladders=False):
     """|dE| of both precisions on the exactly representable cases (8 qubits at chi = 16,
     10 qubits at chi = 32: the bond caps hold the state without truncation), against the
     FP64 oracle energies stored in tests/golden/exact_energies.json by the committed
-    script beside it (the benchmark does not run the oracle here)."""
+    script beside it (the benchmark does not run the oracle here). cancel_ladders: the
+    same through the ladder-cancelling gate list."""
     from paper_2207_03711_gb300 import synthetic as syn
     ref = json.load(open(os.path.join(ROOT, "tests", "golden", "exact_energies.json")))
     out = {}
@@ -254,6 +260,8 @@ def accuracy_probe(G):
         h, g = syn.random_integrals(n // 2, case["integral_seed"])
         H = G.ham_jw_from_integrals(h, g)
         C = G.circ_uccsd(n, ne)
+        if cancel_ladders:
+            G.circ_cancel_ladders(C)
         th = syn.random_amplitudes(C.n_params, case["theta_seed"])
         for name, prec in (("fp64", G.MPS_FP64), ("mixed", G.MPS_MIXED)):
             M = G.mps_create(n, chi, prec)
@@ -325,6 +333,10 @@ def run_ours(args):
     h, g = inputs()
     H = G.ham_jw_from_integrals(h, g)
     C = G.circ_uccsd(N_QUBITS, N_ELEC)
+    cancel = args.circuit == "cancel-ladders"
+    if cancel:
+        G.circ_cancel_ladders(C)
+    n_gates = G.circ_num_gates(C)
     stream = torch.cuda.current_stream().cuda_stream
     K, W = args.steps, max(3, args.warmup)
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
@@ -371,7 +383,7 @@ def run_ours(args):
     # dominant kernel: the gate engine on the FP32 pipes, K thread blocks (one SM each)
     achieved = flops / circ_s / 1e12
     peak = peaks["fp32_tflops"]
-    n_launch = (442272 + 16383) // 16384
+    n_launch = (n_gates + 16383) // 16384
     value = replica_rate(world, K, dev_s)
     cpu_val, cpu_sample, _ = oracle_sample(h, g)
     line = {
@@ -379,6 +391,9 @@ def run_ours(args):
         "steps": K, "warmup": W, "ms_per_step": 1e3 * dev_s / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": dict(WORKLOAD, precision="mixed (complex64 tensors, FP32 SVD, FP64 lambda and sums)",
+                       two_site_gates=n_gates,
+                       circuit=("canonical gate list" if not cancel else
+                                "ladder-cancelling gate list (circ_cancel_ladders): same unitary"),
                        l2="flushed (512 MB write) before the timed call; the K steps run in that one call",
                        steps_in_flight=K,
                        warmup=f"{W} evaluations issued together, {t_warm:.1f} s wall"),
@@ -406,7 +421,7 @@ def run_ours(args):
         "svd_fallbacks_slot0": int(s["n_fallback"]),
         "svd_noconv": int(s["n_svd_noconv"]),
         "discarded_weight_slot0": s["discarded_weight"],
-        "accuracy": accuracy_probe(G),
+        "accuracy": accuracy_probe(G, cancel),
     }
     acc = line["accuracy"]
     line["accuracy_Ha"] = max(acc["abs_dE_Ha_mixed_8q"], acc["abs_dE_Ha_mixed_10q"])
@@ -446,8 +461,8 @@ def tc_peak_tflops():
 def run_config4(args):
     """One step = one full measurement <H> = sum_i a_i <P_i> over all 1 542 657 strings of
     the 64-qubit Hamiltonian on the chi = 256 MPS resident in HBM (mixed precision: the
-    environment contractions of bonds >= 32 on the tensor cores with compensated TF32
-    splits, FP64 sums). Steps run back to back; terms/s = strings x steps / time."""
+    environment contractions of levels whose bonds are both >= 128 on the tensor cores
+    with compensated TF32 splits, FP64 sums). Steps run back to back; terms/s = strings x steps / time."""
     import torch
     import paper_2207_03711_gb300 as G
     from paper_2207_03711_gb300 import synthetic as syn
@@ -465,7 +480,7 @@ def run_config4(args):
     torch.cuda.synchronize()
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     sampler.start()
-    dev_ms, wall_ms, gemm_ms, gemm_fl, launches, gl = [], [], [], [], [], []
+    dev_ms, wall_ms, gemm_ms, gemm_fl, launches, gl, close_ms = [], [], [], [], [], [], []
     energies = []
     for _ in range(K):
         torch.cuda.synchronize()
@@ -475,6 +490,7 @@ def run_config4(args):
         s = G.mps_get_stats(M)
         dev_ms.append(s["ms_measure"])
         gemm_ms.append(s["ms_tc_gemm"])
+        close_ms.append(s["ms_close"])
         gemm_fl.append(s["tc_gemm_flops"])
         launches.append(int(s["kernel_launches"]))
         gl.append(int(s["tc_gemm_launches"]))
@@ -520,6 +536,7 @@ def run_config4(args):
                              "not counted) / summed CUDA-event time of the GEMM launches; the tensor pipe "
                              "executes 3x these flops"},
         "gemm_share_of_step": float(np.sum(gemm_ms)) / float(np.sum(dev_ms)),
+        "close_share_of_step": float(np.sum(close_ms)) / float(np.sum(dev_ms)),
         "cpu_baseline": cpu, "clocks": clocks, "energy_Ha": energies[-1],
         "host_jw_seconds": t_jw,
     }
@@ -542,6 +559,75 @@ def run_config4_tc_case(n_strings, budget_mb=0):
     s = G.mps_get_stats(M)
     print(json.dumps({"config4_tc_case": True, "strings": n_strings, "energy": e, "ms_measure": s["ms_measure"],
                       "tc_gemm_launches": s["tc_gemm_launches"], "tc_gemm_flops": s["tc_gemm_flops"]}))
+
+
+
+def run_config3(args):
+    """32 qubits / 16 electrons, chi = 128, mixed precision; ansatz = all singles and the
+    first 16 doubles of the UCCSD list (13 872 two-site gates); one step = the
+    parameter-shift gradient over those 16 doubles, i.e. the 256 circuits with one of
+    their 128 Pauli rotations shifted by +-pi/2, each followed by a measurement of all
+    strings of the 16-orbital Hamiltonian. The shifted circuits share the unshifted
+    prefix up to their rotation (slot 0 runs it; 256 slots fork from it), so they run in
+    one batched pass. Metric: circuits/s (256 per step)."""
+    import torch
+    import paper_2207_03711_gb300 as G
+    from paper_2207_03711_gb300 import synthetic as syn
+    from paper_2207_03711_gb300.serve import uccsd_circuit
+    G.build()
+    G.load_library()
+    n, ne, chi, nd = 32, 16, 128, 16
+    K, W = args.steps, max(3, args.warmup)
+    h, g = syn.random_integrals(n // 2, SEED)
+    H = G.ham_jw_from_integrals(h, g)
+    n_terms = int(G.ham_get_terms(H)[1].size)
+    C = uccsd_circuit(n, ne, n_doubles=nd)
+    n_singles = 2 * (ne // 2) * ((n - ne) // 2)
+    sel = np.arange(n_singles, n_singles + nd, dtype=np.int32)
+    stream = torch.cuda.current_stream().cuda_stream
+    M = G.mps_create(n, chi, G.MPS_MIXED, n_slots=257, cuda_stream=stream)
+    thetas = [syn.random_amplitudes(C.n_params, 300 + i) for i in range(K + W)]
+    # warm-up steps: the same kernels and slot memory over the first double only (16 of
+    # the 256 circuits), so that W >= 3 warm-ups do not triple the run
+    for w in range(W):
+        G.vqe_gradient(M, C, H, thetas[w], sel[:1], allow_noconv=True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    wall, circ_ms, meas_ms, flops, launches = [], [], [], [], []
+    for k in range(K):
+        t0 = time.perf_counter()
+        grad = G.vqe_gradient(M, C, H, thetas[W + k], sel, allow_noconv=True)
+        wall.append(time.perf_counter() - t0)
+        s = G.mps_get_stats(M)
+        circ_ms.append(s["ms_circuit"])
+        meas_ms.append(s["ms_measure"])
+        flops.append(s["alg_flops_call"])
+        launches.append(int(s["kernel_launches"]))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_dev = (float(np.sum(circ_ms)) + float(np.sum(meas_ms))) * 1e-3
+    peaks = alu_peaks(torch)
+    achieved = float(np.sum(flops)) / (float(np.sum(circ_ms)) * 1e-3) / 1e12
+    n_circ = 2 * 8 * nd
+    line = {"metric": "parameter-shift circuits/s", "value": K * n_circ / t_dev, "unit": "circuits/s", "n_gpus": 1,
+            "steps": K, "warmup": W, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "uccsd_32q_16e_chi128_singles_16doubles_gradient", "qubits": n, "electrons": ne,
+                       "chi": chi, "two_site_gates": G.circ_num_gates(C), "circuits_per_step": n_circ,
+                       "pauli_terms": n_terms, "slots": 257,
+                       "warmup_steps": "gradient over the first double (16 circuits)"},
+            "pauli_terms_per_s": K * n_circ * n_terms / t_dev,
+            "e2e": {"value": K * n_circ / float(np.sum(wall)), "unit": "circuits/s",
+                    "h2d_bytes_per_step": 8 * C.n_params + 4 * nd, "d2h_bytes_per_step": 8 * nd},
+            "gpu_launches": int(np.mean(launches)),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["fp32_tflops"], "traffic": None,
+                         "peak_source": "measured: cuBLAS SGEMM in this process (FP32 CUDA cores)",
+                         "kernel": "k_circuit<float,512> (one block per circuit)"},
+            "breakdown_ms_per_step": {"circuit": float(np.mean(circ_ms)), "measure": float(np.mean(meas_ms))},
+            "gradient_norm": float(np.linalg.norm(grad)), "clocks": clocks}
+    print(json.dumps(line))
 
 
 
@@ -692,6 +778,8 @@ def main():
         run_config4(args)
     elif args.random_gates:
         run_random_gates(args)
+    elif args.config3:
+        run_config3(args)
     elif args.config4_tc_case:
         run_config4_tc_case(args.case_strings, args.case_budget_mb)
     elif args.profile_case:

@@ -38,7 +38,8 @@ class MpsStats(ctypes.Structure):
                 ("cycles", ctypes.c_double * 7), ("n_fallback", ctypes.c_int64),
                 ("alg_flops_total", ctypes.c_double), ("n_nonfinite", ctypes.c_int64),
                 ("alg_flops_call", ctypes.c_double), ("tc_gemm_launches", ctypes.c_int64),
-                ("tc_gemm_flops", ctypes.c_double), ("ms_tc_gemm", ctypes.c_double)]
+                ("tc_gemm_flops", ctypes.c_double), ("ms_tc_gemm", ctypes.c_double),
+                ("ms_close", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -74,6 +75,7 @@ SIGNATURES = {
     "mps_get_stats": [_P, ctypes.POINTER(MpsStats)],
     "mps_destroy": [_P],
     "circ_fuse_gates": [_P, ctypes.POINTER(ctypes.c_int64)],
+    "circ_cancel_ladders": [_P, ctypes.POINTER(ctypes.c_int64)],
     "mps_estimate_bytes": [_I, _I, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_size_t)],
     "mps_apply_gates_noalloc": [_I, _I, _P, _P, _P, _P, _I64, _P, _P, _P, _PD],
     "mps_tc_gemm_tf32x3": [_I, _I, _I, _P, _I64, _P, _I64, _P, _I64, _P],
@@ -239,6 +241,12 @@ def circ_get_rotations(circ):
 def circ_fuse_gates(circ):
     n = ctypes.c_int64(0)
     _check(load_library().circ_fuse_gates(circ, ctypes.byref(n)))
+    return int(n.value)
+
+
+def circ_cancel_ladders(circ):
+    n = ctypes.c_int64(0)
+    _check(load_library().circ_cancel_ladders(circ, ctypes.byref(n)))
     return int(n.value)
 
 

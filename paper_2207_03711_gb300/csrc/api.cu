@@ -136,6 +136,7 @@ struct mps_s {
   // optional per-launch timing of the tensor-core GEMMs (mps_set_kernel_timing)
   bool ktime = false;
   std::vector<cudaEvent_t> kev;
+  std::vector<uint8_t> kev_kind;   // per used pair: 0 tensor-core GEMM, 1 close
   size_t kev_used = 0;
   size_t tc_floats = 0;
   double* d_theta = nullptr;
@@ -235,20 +236,7 @@ static int finish_circ(int n, std::vector<Rotation> rots, int n_params, circ_t* 
   c->comp.n_params = n_params;
   compile_rotations(n, rots, &c->comp);
   c->comp.reference.assign(n, 0);
-  // gate carrying the rotation angle: the single gate (|S| = 1) or the top gate
-  const auto& R = c->comp.rotations;
-  c->rot_param_gate.assign(R.size(), -1);
-  for (size_t r = 0; r < R.size(); ++r) {
-    int lo = -1, hi = -1, w = 0;
-    for (int q = 0; q < n; ++q)
-      if (R[r].code[q]) {
-        if (lo < 0) lo = q;
-        hi = q;
-        ++w;
-      }
-    if (w == 0) continue;
-    c->rot_param_gate[r] = c->comp.rot_first_gate[r] + (w == 1 ? 0 : (hi - lo - 1));
-  }
+  c->rot_param_gate = param_gates(c->comp);
   *out = c.release();
   return MPS_OK;
 }
@@ -463,9 +451,11 @@ struct MeasWalk {
 };
 
 // The next pair of timing events (created on first use) when kernel timing is on.
-static int next_event_pair(mps_s* m, cudaEvent_t* e0, cudaEvent_t* e1) {
+static int next_event_pair(mps_s* m, cudaEvent_t* e0, cudaEvent_t* e1, uint8_t kind = 0) {
   *e0 = *e1 = nullptr;
   if (!m->ktime) return MPS_OK;
+  m->kev_kind.resize(m->kev_used / 2 + 1);
+  m->kev_kind[m->kev_used / 2] = kind;
   while (m->kev.size() < m->kev_used + 2) {
     cudaEvent_t e;
     CU(cudaEventCreate(&e));
@@ -508,8 +498,12 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
   const int64_t cs = std::lower_bound(cn.begin(), cn.end(), u0) - cn.begin();
   const int64_t ce = std::lower_bound(cn.begin(), cn.end(), u1) - cn.begin();
   if (ce > cs) {
+    cudaEvent_t e0, e1;
+    TRY(next_event_pair(m, &e0, &e1, 1));
+    if (e0) CU(cudaEventRecord(e0, m->st));
     CU(launch_env_close(m->dm, m->prec, c.slot, k, T, m->w.Bhat, c.h->d_cnode[k] + cs, c.h->d_cletter[k] + cs,
                         c.h->d_cterm[k] + cs, (int)(ce - cs), u0, m->w.vals, m->st));
+    if (e1) CU(cudaEventRecord(e1, m->st));
     ++c.launches;
   }
   if (k + 1 >= t.n_levels || k + 1 >= m->n) return MPS_OK;
@@ -581,7 +575,7 @@ static int run_measure(mps_s* m, ham_s* h, int slot, double* out_host, bool term
   for (size_t i = 0; i + 1 < m->kev_used; i += 2) {
     float t = 0;
     CU(cudaEventElapsedTime(&t, m->kev[i], m->kev[i + 1]));
-    m->stats.ms_tc_gemm += t;
+    (m->kev_kind[i / 2] ? m->stats.ms_close : m->stats.ms_tc_gemm) += t;
   }
   if (tc_err) return fail(MPS_ETIMEOUT, "a bounded wait of the tensor-core GEMM pipeline ran out");
   return MPS_OK;
@@ -719,6 +713,19 @@ int circ_fuse_gates(circ_t c, int64_t* n_gates) {
   c->d_mats = nullptr;
   if (n_gates) *n_gates = (int64_t)c->comp.gates.size();
   return MPS_OK;
+}
+
+int circ_cancel_ladders(circ_t c, int64_t* n_gates) {
+  if (!c) return fail(MPS_EINVAL, "circ_cancel_ladders: null handle");
+  std::vector<Rotation> rots = c->comp.rotations;
+  order_for_ladder_cancellation(&rots);
+  const int np = c->comp.n_params;
+  std::vector<uint8_t> ref = c->comp.reference;
+  compile_rotations(c->comp.n, rots, &c->comp);
+  c->comp.n_params = np;
+  c->comp.reference = ref;
+  c->rot_param_gate = param_gates(c->comp);
+  return circ_fuse_gates(c, n_gates);
 }
 
 int circ_destroy(circ_t c) {

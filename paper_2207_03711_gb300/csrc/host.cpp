@@ -450,6 +450,62 @@ void fuse_gates(Compiled* c, std::vector<int64_t>* param_gate) {
   c->rot_first_gate = std::move(first);
 }
 
+static bool pauli_commute(const std::vector<uint8_t>& a, const std::vector<uint8_t>& b) {
+  int anti = 0;
+  for (size_t q = 0; q < a.size(); ++q) anti += (a[q] && b[q] && a[q] != b[q]);
+  return (anti & 1) == 0;
+}
+
+int64_t order_for_ladder_cancellation(std::vector<Rotation>* rots) {
+  std::vector<Rotation>& R = *rots;
+  int64_t changed = 0;
+  size_t i = 0;
+  while (i < R.size()) {
+    size_t j = i + 1;
+    while (j < R.size() && R[i].param >= 0 && R[j].param == R[i].param) ++j;
+    bool commuting = true;
+    for (size_t a = i; a < j && commuting; ++a)
+      for (size_t b = a + 1; b < j && commuting; ++b) commuting = pauli_commute(R[a].code, R[b].code);
+    if (j - i > 1 && commuting) {
+      // the letters from the lowest non-identity site up; runs of one excitation share
+      // their support, so this is a lexicographic order of the letters on it
+      auto key = [](const Rotation& r) {
+        size_t lo = 0;
+        while (lo < r.code.size() && !r.code[lo]) ++lo;
+        return std::vector<uint8_t>(r.code.begin() + (std::ptrdiff_t)lo, r.code.end());
+      };
+      std::vector<Rotation> run(R.begin() + (std::ptrdiff_t)i, R.begin() + (std::ptrdiff_t)j);
+      std::stable_sort(run.begin(), run.end(), [&](const Rotation& x, const Rotation& y) { return key(x) < key(y); });
+      bool same = true;
+      for (size_t t = 0; t < run.size(); ++t) same = same && run[t].code == R[i + t].code;
+      if (!same) {
+        std::copy(run.begin(), run.end(), R.begin() + (std::ptrdiff_t)i);
+        ++changed;
+      }
+    }
+    i = j;
+  }
+  return changed;
+}
+
+std::vector<int64_t> param_gates(const Compiled& c) {
+  // the single gate (one non-identity site) or the top gate of the ladder
+  const auto& R = c.rotations;
+  std::vector<int64_t> pg(R.size(), -1);
+  for (size_t r = 0; r < R.size(); ++r) {
+    int lo = -1, hi = -1, w = 0;
+    for (int q = 0; q < c.n; ++q)
+      if (R[r].code[q]) {
+        if (lo < 0) lo = q;
+        hi = q;
+        ++w;
+      }
+    if (w == 0) continue;
+    pg[r] = c.rot_first_gate[r] + (w == 1 ? 0 : (hi - lo - 1));
+  }
+  return pg;
+}
+
 void gate_matrix(const Compiled& c, const GateRec& g, const double* theta, cd* U) {
   M4 a;
   std::copy(c.mats.begin() + 16 * (size_t)g.m0, c.mats.begin() + 16 * (size_t)g.m0 + 16, a.begin());

@@ -104,6 +104,17 @@ void compile_rotations(int n, const std::vector<Rotation>& rots, Compiled* out);
 // the index of each rotation's parametric gate (-1 if it has none); rot_first_gate is
 // rewritten to the first gate that carries each rotation's work.
 void fuse_gates(Compiled* c, std::vector<int64_t>* param_gate);
+// Reorders the rotations inside every run of consecutive rotations that share one
+// parameter and commute pairwise (the Pauli strings of one excitation's generator, whose
+// exponentials commute, so the product is the same in any order): ascending by their
+// letters read from the lowest non-identity site up. Consecutive rotations then agree on
+// their lowest sites, where one's descending CNOT ladder meets the next one's ascending
+// ladder, and fuse_gates cancels those ladder segments pair by pair. Returns the number
+// of runs whose order changed.
+int64_t order_for_ladder_cancellation(std::vector<Rotation>* rots);
+// Gate of each rotation that carries its angle (-1 for a rotation without gates) in a
+// list made by compile_rotations.
+std::vector<int64_t> param_gates(const Compiled& c);
 // Host evaluation of a gate matrix for a given theta (inspection only).
 void gate_matrix(const Compiled& c, const GateRec& g, const double* theta, cd* U);
 

@@ -13,6 +13,7 @@
 // to T = Q B P^H with Q = H_0 H_1 ... and P = G_0 G_1 ...; reflector k's tail is
 // (unscaled tail stored in T) x (scale stored over its pivot), see bidiagonalize.
 #pragma once
+#include <cfloat>
 #include "cx.cuh"
 
 namespace mpsvqe {
@@ -26,16 +27,23 @@ __device__ __forceinline__ R rabs(R x) {
 __device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
 
-// LAPACK-style reflector for x = (alpha, tail) with ||tail||^2 = xn2.
+// LAPACK-style reflector for x = (alpha, tail) with ||tail||^2 = xn2. A vector whose
+// squared norm is within 16x of the smallest normal number counts as zero: the squares
+// that make up that norm have lost their bits to underflow (entries below ~5e-19 in
+// FP32, ~6e-154 in FP64), so the norm could come out as 0 while alpha is not, and
+// 1 / (alpha - beta) would be a division by zero. The identity is taken there and the
+// entries (absolutely that small) are dropped from the bidiagonal.
 template <class R>
 __device__ __forceinline__ void make_reflector(Cx<R> alpha, R xn2, Cx<R>* tau, R* beta, Cx<R>* scale) {
-  if (xn2 == R(0) && alpha.y == R(0)) {
+  constexpr R kTiny2 = R(16) * (sizeof(R) == 4 ? R(FLT_MIN) : R(DBL_MIN));
+  const R n2 = alpha.x * alpha.x + alpha.y * alpha.y + xn2;
+  if ((xn2 == R(0) && alpha.y == R(0)) || !(n2 > kTiny2)) {
     *tau = cx<R>(0, 0);
     *beta = alpha.x;
     *scale = cx<R>(0, 0);
     return;
   }
-  const R nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+  const R nrm = sqrt(n2);
   const R b = alpha.x >= R(0) ? -nrm : nrm;
   *beta = b;
   *tau = cx<R>((b - alpha.x) / b, -alpha.y / b);

@@ -280,6 +280,25 @@ def test_edge_sizes_random_gates(n, chi):
     assert np.abs(ev_g - ev_o).max() <= 1e-11
 
 
+@pytest.mark.parametrize("prec,dust", [(G.MPS_MIXED, 1e-25), (G.MPS_FP64, 1e-170)])
+def test_gate_on_entries_whose_squares_underflow(prec, dust):
+    """Rounding dust in a sector that is empty in exact arithmetic can leave a column
+    of M' whose entries are tiny but not zero, so small that their squares underflow:
+    its norm comes out 0 while its leading entry is not. The reflector of the
+    bidiagonalisation must take that column as zero (not divide by it), and the state
+    must stay finite: |0>(|0> + i dust |1>) through three identity gates ends as |00>."""
+    M = G.mps_create(2, 4, prec)
+    s0 = np.array([1.0, 0.0], dtype=complex).reshape(1, 2, 1)
+    s1 = np.array([1.0, 1j * dust], dtype=complex).reshape(1, 2, 1)
+    G.mps_set_state(M, [s0, s1], [np.array([1.0])])
+    G.mps_apply_gates(M, np.zeros(3, dtype=np.int32), np.tile(np.eye(4, dtype=complex), (3, 1, 1)))
+    r, sites, lams = G.mps_get_state(M)
+    assert all(np.all(np.isfinite(x)) for x in sites) and all(np.all(np.isfinite(x)) for x in lams)
+    psi = np.einsum("aib,bjc->ij", sites[0], sites[1])
+    assert abs(abs(psi[0, 0]) - 1.0) <= 1e-6
+    assert np.abs(psi).ravel()[1:].max() <= 1e-6
+
+
 def test_empty_circuit_and_duplicate_strings():
     n = 6
     C = G.circ_create(np.zeros((0, n), dtype=np.uint8), np.zeros(0, dtype=np.int32), np.zeros(0))
@@ -408,3 +427,28 @@ def test_fused_circuit_variant():
     g0 = G.vqe_gradient(M, C0, H, theta, sel)
     g1 = G.vqe_gradient(M, C1, H, theta, sel)
     assert np.abs(g0 - g1).max() <= 1e-9
+
+
+@pytest.mark.parametrize("prec,tol", [(G.MPS_FP64, FP64_E_TOL), (G.MPS_MIXED, MIXED_E_TOL_8Q)])
+def test_ladder_cancellation_variant(prec, tol):
+    """The ladder-cancelling gate list (circ_cancel_ladders, 943 instead of 1568 gates at
+    8 qubits) is the same circuit: untruncated energies equal the oracle's within each
+    precision's bound, and FP64 parameter-shift gradients equal the canonical list's."""
+    n, ne, chi = 8, 4, 16
+    h, g = syn.random_integrals(4, 0)
+    codes, coeffs = pauli.jordan_wigner_hamiltonian(h, g)
+    rc, rp, rs, _ = ucc.uccsd_rotations(n, ne)
+    H = G.ham_jw_from_integrals(h, g)
+    C0, C1 = G.circ_uccsd(n, ne), G.circ_uccsd(n, ne)
+    assert G.circ_cancel_ladders(C1) < 0.7 * G.circ_num_gates(C0)
+    theta = syn.random_amplitudes(C0.n_params, 0)
+    e_sv = sv.energy(sv.run_ansatz(n, ne, rc, rp, rs, theta), codes, coeffs)[0]
+    M = G.mps_create(n, chi, prec, n_slots=9)
+    e1 = G.vqe_energy(M, C1, H, theta)
+    print(f"8q ladder-cancelled prec={prec} |dE| = {abs(e1 - e_sv):.3e} Ha")
+    assert abs(e1 - e_sv) <= tol
+    if prec == G.MPS_FP64:
+        sel = [0, 5, C0.n_params - 1]
+        g0 = G.vqe_gradient(M, C0, H, theta, sel)
+        g1 = G.vqe_gradient(M, C1, H, theta, sel)
+        assert np.abs(g0 - g1).max() <= 1e-9
