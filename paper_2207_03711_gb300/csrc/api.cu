@@ -163,6 +163,7 @@ struct mps_s {
     dfree(d_site_off, st);
     dfree(w.R, st);
     dfree(w.Bhat, st);
+    dfree(w.Q, st);
     for (void* p : lvl_L) dfree(p, st);
     for (void* p : lvl_T) dfree(p, st);
     dfree(tc.scratch, st);
@@ -290,7 +291,7 @@ static MeasPlan meas_plan(const Trie& t, int chi, size_t es, bool mixed, size_t 
     p.level_bytes += (size_t)p.cap[k] * node_bytes;
   }
   if (mixed && chi >= kTcMinDim) {
-    const size_t per_node = 96 * chi2;    // float planes and GEMM outputs per node
+    const size_t per_node = 24 * chi2;    // bytes of the W rows and GEMM-C output per child
     // a quarter of an explicit budget, else 1 GiB (chi <= 128) or 4 GiB
     const size_t tc_budget = explicit_budget ? std::max<size_t>(size_t(64) << 20, budget / 4)
                                              : (chi <= 128 ? size_t(1) : size_t(4)) << 30;
@@ -310,6 +311,8 @@ static int ensure_meas(mps_s* m, ham_s* h) {
     m->w.R = p;
     TRY(dev_alloc(&p, (size_t)m->dm.slot_elems * m->es, "B-hat", m->st));
     m->w.Bhat = p;
+    TRY(dev_alloc(&p, (size_t)m->n * 4 * chi2 * m->es, "per-letter right blocks", m->st));
+    m->w.Q = p;
   }
   const MeasPlan plan = meas_plan(h->trie, m->chi, m->es, m->prec == MPS_MIXED, m->meas_budget);
   m->lvl_L.resize(m->n, nullptr);
@@ -471,7 +474,6 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
   mps_s* m = c.m;
   const Trie& t = c.h->trie;
   const int U = u1 - u0, D = c.r[k], Dp = c.r[k + 1];
-  const size_t chi2 = (size_t)m->chi * m->chi;
   void* L = m->lvl_L[k];
   void* T = m->lvl_T[k];
   const bool tc = m->prec == MPS_MIXED && m->tc.scratch && D >= kTcMinDim && Dp >= kTcMinDim;
@@ -479,16 +481,12 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
     const Cx<float>* Bk = (const Cx<float>*)m->dm.B + (size_t)c.slot * m->dm.slot_elems + m->site_off[k];
     CU(env_tc_site(m->tc, Bk, D, Dp, m->st));
     ++c.launches;
-    for (int s0 = 0; s0 < U; s0 += m->tc.max_nodes) {
-      const int ns = std::min(m->tc.max_nodes, U - s0);
-      cudaEvent_t e0, e1;
-      TRY(next_event_pair(m, &e0, &e1));
-      CU(env_tc_T(m->tc, (const Cx<float>*)L + (size_t)s0 * chi2, (Cx<float>*)T + (size_t)s0 * 2 * chi2, ns, D, Dp,
-                  m->st, e0, e1));
-      c.launches += 3;
-      m->stats.tc_gemm_launches += 1;
-      m->stats.tc_gemm_flops += 2.0 * ((double)ns * D) * (4.0 * Dp) * (2.0 * D);
-    }
+    cudaEvent_t e0, e1;
+    TRY(next_event_pair(m, &e0, &e1));
+    CU(env_tc_T(m->tc, (const Cx<float>*)L, (Cx<float>*)T, U, D, Dp, m->st, e0, e1));
+    c.launches += 1;
+    m->stats.tc_gemm_launches += 1;
+    m->stats.tc_gemm_flops += 2.0 * ((double)U * D) * (4.0 * Dp) * (2.0 * D);
   } else {
     CU(launch_env_T(m->dm, m->prec, c.slot, k, L, T, U, m->st));
     ++c.launches;
@@ -501,7 +499,7 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
     cudaEvent_t e0, e1;
     TRY(next_event_pair(m, &e0, &e1, 1));
     if (e0) CU(cudaEventRecord(e0, m->st));
-    CU(launch_env_close(m->dm, m->prec, c.slot, k, T, m->w.Bhat, c.h->d_cnode[k] + cs, c.h->d_cletter[k] + cs,
+    CU(launch_env_close(m->dm, m->prec, c.slot, k, L, m->w.Q, c.h->d_cnode[k] + cs, c.h->d_cletter[k] + cs,
                         c.h->d_cterm[k] + cs, (int)(ce - cs), u0, m->w.vals, m->st));
     if (e1) CU(cudaEventRecord(e1, m->st));
     ++c.launches;
@@ -512,7 +510,7 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
   const int64_t c1 = std::lower_bound(par.begin(), par.end(), u1) - par.begin();
   while (a < c1) {
     int64_t b = a + 1;
-    while (b < c1 && b - a < m->lvl_cap[k + 1] && (!tc || par[b] - par[a] < m->tc.max_nodes)) ++b;
+    while (b < c1 && b - a < m->lvl_cap[k + 1] && (!tc || b - a < m->tc.max_nodes)) ++b;
     if (tc) {
       // the shared operands of site k live in the scratch, which the deeper levels of
       // the previous sub-chunk have used for their own sites: rebuild them
@@ -521,13 +519,12 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
       ++c.launches;
       cudaEvent_t e0, e1;
       TRY(next_event_pair(m, &e0, &e1));
-      const int np = par[b - 1] - par[a] + 1;
-      CU(env_tc_children(m->tc, (const Cx<float>*)T, par[a] - u0, par[b - 1] - u0 + 1, D, Dp,
-                         c.h->d_parent[k + 1] + a, c.h->d_edge[k + 1] + a, (int)(b - a), u0,
-                         (Cx<float>*)m->lvl_L[k + 1], m->st, e0, e1));
+      const int nch = (int)(b - a);
+      CU(env_tc_children(m->tc, (const Cx<float>*)T, c.h->d_parent[k + 1] + a, c.h->d_edge[k + 1] + a, nch, u0,
+                         D, Dp, (Cx<float>*)m->lvl_L[k + 1], m->st, e0, e1));
       c.launches += 3;
       m->stats.tc_gemm_launches += 1;
-      m->stats.tc_gemm_flops += 2.0 * (4.0 * Dp) * ((double)np * 2 * Dp) * (2.0 * D);
+      m->stats.tc_gemm_flops += 2.0 * (2.0 * Dp) * ((double)nch * Dp) * (4.0 * D);
     } else {
       CU(launch_env_child(m->dm, m->prec, c.slot, k, T, c.h->d_parent[k + 1] + a, c.h->d_edge[k + 1] + a,
                           (int)(b - a), u0, m->lvl_L[k + 1], m->st));
@@ -754,6 +751,7 @@ int mps_estimate_bytes(int n_qubits, int chi, int precision, int n_slots, circ_t
              + S * (8 + 16 + 64 + n + 24) + (size_t)n * 8;
   const size_t chi2 = (size_t)chi * chi;
   b += (size_t)(n + 1) * chi2 * es + slot * es;     // right environments, B-hat
+  b += (size_t)n * 4 * chi2 * es;                   // per-letter right blocks
   if (circ) b += circ->comp.gates.size() * sizeof(GateRec) + circ->comp.mats.size() * 16 +
                  S * std::max(1, circ->comp.n_params) * 8;
   if (ham) {

@@ -1,23 +1,30 @@
 // Environment contractions of the trie measurement on the tensor cores (mixed precision).
 //
 // One trie level k (site k, left bond D = D_k, right bond D' = D_{k+1}) does two dense
-// complex contractions per node (Eq. 11 generalised to Pauli strings, Sec. III-C):
-//   T_j[u] = L[u] B^j                         (D x D)(D x D'),  j = 0, 1
-//   C_ij[u] = (B^i)^+ T_j[u]                  (D' x D)(D x D'), i, j = 0, 1
-// and a child with letter P on its edge takes L[child] = sum_ij P_ij C_ij[parent]. Over
-// a chunk of U nodes both become single real GEMMs with a shared operand built from the
-// site tensor (split-complex: real and imaginary planes side by side along K):
-//   GEMM-T: rows (u, a) of [Re L | Im L]  (U D x 2D)  times  BT (4D' x 2D)^T
-//           BT row (j, re, c) = [ Re B^j[:, c], -Im B^j[:, c] ],
-//           BT row (j, im, c) = [ Im B^j[:, c],  Re B^j[:, c] ]
-//   GEMM-C: AC (4D' x 2D) times rows (u, j, c) of [Re T_j[u][:, c] | Im T_j[u][:, c]]^T
-//           AC row (i, re, c') = [ Re B^i[:, c'],  Im B^i[:, c'] ],
-//           AC row (i, im, c') = [-Im B^i[:, c'],  Re B^i[:, c'] ]
+// complex contractions (Eq. 11 generalised to Pauli strings, Sec. III-C):
+//   T_j[u] = L[u] B^j                               (D x D)(D x D'),  j = 0, 1
+//   L[child] = sum_ij P_ij (B^i)^+ T_j[u]          P = the edge letter of the child
+// The second is formed per child, not per parent: with W_i = sum_j P_ij T_j[u] (for
+// I: (T_0, T_1); X: (T_1, T_0); Y: (-i T_1, i T_0); Z: (T_0, -T_1)) it is one product
+// sum_i (B^i)^+ W_i with the i sum stacked along K. In a Jordan-Wigner trie almost every
+// parent has a single child (the next letter of a Z chain), and computing the four
+// C_ij = (B^i)^+ T_j of every parent, as a per-parent form would, doubles that work.
+// Over a chunk both become single real GEMMs with a shared operand built from the site
+// tensor:
+//   GEMM-T: rows (u, a) of L[u] read as interleaved floats (re, im per entry; U D x 2D),
+//           the level buffer itself, times BT (4D' x 2D)^T with
+//           BT row (j, c, re) = [ Re B^j[b, c], -Im B^j[b, c] ]_b   (interleaved per b),
+//           BT row (j, c, im) = [ Im B^j[b, c],  Re B^j[b, c] ]_b,
+//           so that output row (u, a) is [T_0[u][a][:] | T_1[u][a][:]] as interleaved
+//           complex: the GEMM writes the level's T buffer directly.
+//   GEMM-C: A2 (2D' x 4D) times rows (child, c) of
+//           [Re W_0[:, c] | Im W_0[:, c] | Re W_1[:, c] | Im W_1[:, c]]^T
+//           A2 row (re, c') = [ Re B^0[:, c'],  Im B^0[:, c'],  Re B^1[:, c'],  Im B^1[:, c'] ],
+//           A2 row (im, c') = [-Im B^0[:, c'],  Re B^0[:, c'], -Im B^1[:, c'],  Re B^1[:, c'] ]
 // Both run on tc::launch_gemm_tf32x3 (tcgen05, compensated TF32 splits made inside the
-// GEMM from the FP32 tiles it loads). The kernels here build the FP32 operand planes and
-// move results between the GEMM layouts and
-// the complex environment buffers that the rest of the measurement uses (L: node u at
-// u chi^2, leading dimension D; T: T_j[u] at (2u + j) chi^2, leading dimension D').
+// GEMM from the FP32 tiles it loads). Level buffers are dense: L[u] at u D^2 (leading
+// dimension D); on this route T_j[u][a][c] at ((u D + a) 2 + j) D' + c. The kernels here
+// build the site operands and the W rows and place the children's environments.
 #include <cstdint>
 
 #include "cx.cuh"
@@ -26,125 +33,84 @@
 
 namespace mpsvqe {
 
-__host__ __device__ inline int64_t round4(int64_t x) { return (x + 3) & ~(int64_t)3; }
-
 // ---------------------------------------------------------------- operand planes
-// [Re L[u][a][:] | Im L[u][a][:]] for rows (u, a), leading dimension ldk.
-__global__ void k_tc_pack_L(const Cx<float>* L, int64_t chi2, int U, int D, float* out, int64_t ldk) {
-  const int64_t total = (int64_t)U * D * ldk;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i / ldk, col = i - row * ldk;
-    const int u = (int)(row / D), a = (int)(row - (int64_t)u * D);
-    float v = 0.f;
-    if (col < 2 * D) {
-      const Cx<float> z = L[(size_t)u * chi2 + (size_t)a * D + (col < D ? col : col - D)];
-      v = col < D ? z.x : z.y;
+// BT (4D' x 2D) and A2 (2D' x 4D) from site k (B[b][j][c] at (b 2 + j) D' + c).
+__global__ void k_tc_site_operands(const Cx<float>* Bk, int D, int Dp, float* bt, float* a2) {
+  const int64_t nbt = (int64_t)4 * Dp * 2 * D, na2 = (int64_t)2 * Dp * 4 * D;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbt + na2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < nbt) {
+      const int64_t row = i / (2 * D);
+      const int col = (int)(i - row * 2 * D);
+      const int ro = (int)(row & 1), c = (int)((row >> 1) % Dp), j = (int)((row >> 1) / Dp);
+      const int b = col >> 1, ri = col & 1;
+      const Cx<float> z = Bk[((size_t)b * 2 + j) * Dp + c];   // B^j[b][c]
+      // re row: (Br, -Bi) per b; im row: (Bi, Br) per b
+      bt[i] = ro == 0 ? (ri == 0 ? z.x : -z.y) : (ri == 0 ? z.y : z.x);
+    } else {
+      const int64_t e = i - nbt, row = e / (4 * D);
+      const int col = (int)(e - row * 4 * D);
+      const int ro = (int)(row / Dp), cp = (int)(row % Dp);
+      const int ii = col / (2 * D), ri = (col / D) & 1, a = col % D;
+      const Cx<float> z = Bk[((size_t)a * 2 + ii) * Dp + cp];   // B^i[a][c']
+      // re row [Br, Bi] per i, im row [-Bi, Br] per i
+      a2[e] = ro == 0 ? (ri == 0 ? z.x : z.y) : (ri == 0 ? -z.y : z.x);
     }
-    out[i] = v;
   }
 }
 
-// BT (4D' x ldk) and AC (4D' x ldk) from site k (B[b][j][c] at (b 2 + j) D' + c).
-__global__ void k_tc_site_operands(const Cx<float>* Bk, int D, int Dp, int64_t ldk, float* bt, float* ac) {
-  const int64_t total = (int64_t)4 * Dp * ldk;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = i / ldk;
-    const int col = (int)(i - row * ldk);
-    const int j = (int)(row / (2 * Dp)), ro = (int)((row / Dp) & 1), c = (int)(row % Dp);
-    float vt = 0.f, va = 0.f;
-    if (col < 2 * D) {
-      const int ri = col >= D, b = ri ? col - D : col;
-      const Cx<float> z = Bk[((size_t)b * 2 + j) * Dp + c];   // B^j[b][c] (also B^i[a][c'] with i = j)
-      // BT: re row [Br, -Bi], im row [Bi, Br]
-      vt = ro == 0 ? (ri == 0 ? z.x : -z.y) : (ri == 0 ? z.y : z.x);
-      // AC: re row [Br, Bi], im row [-Bi, Br]
-      va = ro == 0 ? (ri == 0 ? z.x : z.y) : (ri == 0 ? -z.y : z.x);
-    }
-    bt[i] = vt;
-    ac[i] = va;
-  }
-}
-
-// C_T (U D x 4D', rows (u, a), columns (j, re/im, c)) -> T_j[u][a][c] complex.
-__global__ void k_tc_scatter_T(const float* CT, int U, int D, int Dp, Cx<float>* T, int64_t chi2) {
-  const int64_t total = (int64_t)U * 2 * D * Dp;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(i % Dp);
-    int64_t r = i / Dp;
-    const int a = (int)(r % D);
-    r /= D;
-    const int j = (int)(r & 1);
-    const int u = (int)(r >> 1);
-    const float* row = CT + ((int64_t)u * D + a) * 4 * Dp;
-    T[((size_t)u * 2 + j) * chi2 + (size_t)a * Dp + c] = cx<float>(row[(2 * j) * Dp + c], row[(2 * j + 1) * Dp + c]);
-  }
-}
-
-// Rows (u - pa, j, c) of [Re T_j[u][:, c] | Im T_j[u][:, c]] for parents u in [pa, pb):
-// a transpose of each D x D' block through 32 x 32 shared-memory tiles.
-__global__ void k_tc_pack_TT(const Cx<float>* T, int64_t chi2, int pa, int D, int Dp, float* out, int64_t ldk) {
-  __shared__ Cx<float> tile[32][33];
-  const int blk = blockIdx.z;               // (u - pa) * 2 + j
-  const int u = pa + (blk >> 1), j = blk & 1;
+// Rows (child, c) of [Re W_0[:, c] | Im W_0[:, c] | Re W_1[:, c] | Im W_1[:, c]] (leading
+// dimension 4D) for children [0, nc), W_i = sum_j P_ij T_j[parent] with P the child's
+// edge letter: a transpose of the parent's two D x D' blocks through 32 x 32 shared-memory
+// tiles, mixed per letter on the way out.
+__global__ void k_tc_pack_W(const Cx<float>* T, const int32_t* parent, const uint8_t* edge, int node_base, int D,
+                            int Dp, float* out) {
+  __shared__ Cx<float> t0[32][33];
+  __shared__ Cx<float> t1[32][33];
+  const int ch = blockIdx.z;
+  const int u = parent[ch] - node_base;
+  const uint8_t lt = edge[ch];
   const int a0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-  const Cx<float>* Tj = T + ((size_t)u * 2 + j) * chi2;
+  const Cx<float>* Tu = T + (size_t)u * 2 * D * Dp;   // row a: [T_0[u][a][:] | T_1[u][a][:]]
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
     const int a = a0 + y, c = c0 + threadIdx.x;
-    tile[y][threadIdx.x] = (a < D && c < Dp) ? Tj[(size_t)a * Dp + c] : cx<float>(0.f, 0.f);
+    const bool in = a < D && c < Dp;
+    t0[y][threadIdx.x] = in ? Tu[(size_t)a * 2 * Dp + c] : cx<float>(0.f, 0.f);
+    t1[y][threadIdx.x] = in ? Tu[(size_t)a * 2 * Dp + Dp + c] : cx<float>(0.f, 0.f);
   }
   __syncthreads();
+  const int64_t ldk = 4 * (int64_t)D;
   for (int y = threadIdx.y; y < 32; y += blockDim.y) {
     const int c = c0 + y, a = a0 + threadIdx.x;
     if (c < Dp && a < D) {
-      const Cx<float> z = tile[threadIdx.x][y];
-      const int64_t row = ((int64_t)blk * Dp + c) * ldk;
-      out[row + a] = z.x;
-      out[row + D + a] = z.y;
-    }
-  }
-  // zero padding columns 2D..ldk-1 of the rows this block owns (first a-tile only)
-  if (blockIdx.y == 0) {
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-      const int c = c0 + y;
-      if (c < Dp)
-        for (int col = 2 * D + threadIdx.x; col < ldk; col += 32) {
-          const int64_t row = ((int64_t)blk * Dp + c) * ldk;
-          out[row + col] = 0.f;
-        }
+      const Cx<float> x0 = t0[threadIdx.x][y], x1 = t1[threadIdx.x][y];
+      Cx<float> w0, w1;
+      switch (lt) {
+        case 0: w0 = x0; w1 = x1; break;                                        // I
+        case 1: w0 = x1; w1 = x0; break;                                        // X
+        case 2: w0 = cx<float>(x1.y, -x1.x); w1 = cx<float>(-x0.y, x0.x); break;  // Y: -i T_1, i T_0
+        default: w0 = x0; w1 = cx<float>(-x1.x, -x1.y); break;                  // Z
+      }
+      float* row = out + ((int64_t)ch * Dp + c) * ldk;
+      row[a] = w0.x;
+      row[D + a] = w0.y;
+      row[2 * D + a] = w1.x;
+      row[3 * D + a] = w1.y;
     }
   }
 }
 
-// Children [0, nc): L[child][c'][c] = sum_e s_e C_{i_e j_e}[parent][c'][c], with
-// C_L (4D' x ldc), rows (i, re/im, c'), columns ((u - pa), j, c).
-__global__ void k_tc_combine(const float* CL, int64_t ldc, int Dp, const int32_t* parent, const uint8_t* edge,
-                             int nc, int node_base, int pa, Cx<float>* Lout, int64_t chi2) {
-  const int64_t total = (int64_t)nc * Dp * Dp;
+// Children [0, nc): L[child][c'][c] from C_L (2D' x nc D'), rows (re/im, c'), columns
+// (child, c).
+__global__ void k_tc_place(const float* CL, int Dp, int nc, Cx<float>* Lout) {
+  const int64_t total = (int64_t)nc * Dp * Dp, N = (int64_t)nc * Dp;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(i % Dp);
     const int64_t r = i / Dp;
     const int cp = (int)(r % Dp);
     const int ch = (int)(r / Dp);
-    const int u = parent[ch] - node_base - pa;
-    const uint8_t lt = edge[ch];
-    // letter -> (i, j, s) pairs: I: (0,0,1)(1,1,1); X: (0,1,1)(1,0,1); Y: (0,1,-i)(1,0,i); Z: (0,0,1)(1,1,-1)
-    int ii[2], jj[2];
-    Cx<float> sg[2];
-    switch (lt) {
-      case 0: ii[0] = 0; jj[0] = 0; sg[0] = cx<float>(1, 0); ii[1] = 1; jj[1] = 1; sg[1] = cx<float>(1, 0); break;
-      case 1: ii[0] = 0; jj[0] = 1; sg[0] = cx<float>(1, 0); ii[1] = 1; jj[1] = 0; sg[1] = cx<float>(1, 0); break;
-      case 2: ii[0] = 0; jj[0] = 1; sg[0] = cx<float>(0, -1); ii[1] = 1; jj[1] = 0; sg[1] = cx<float>(0, 1); break;
-      default: ii[0] = 0; jj[0] = 0; sg[0] = cx<float>(1, 0); ii[1] = 1; jj[1] = 1; sg[1] = cx<float>(-1, 0); break;
-    }
-    Cx<float> acc = cx<float>(0.f, 0.f);
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int64_t col = ((int64_t)u * 2 + jj[e]) * Dp + c;
-      const float re = CL[((int64_t)(2 * ii[e]) * Dp + cp) * ldc + col];
-      const float im = CL[((int64_t)(2 * ii[e] + 1) * Dp + cp) * ldc + col];
-      acc = acc + sg[e] * cx<float>(re, im);
-    }
-    Lout[(size_t)ch * chi2 + (size_t)cp * Dp + c] = acc;
+    const int64_t col = (int64_t)ch * Dp + c;
+    Lout[((size_t)ch * Dp + cp) * Dp + c] = cx<float>(CL[(int64_t)cp * N + col], CL[(int64_t)(Dp + cp) * N + col]);
   }
 }
 
@@ -154,42 +120,37 @@ static inline int grid_for(int64_t total) {
 }
 
 size_t env_tc_scratch_floats(int chi, int max_nodes) {
-  const int64_t D = chi, Dp = chi, U = max_nodes, ldk = round4(2 * D);
-  const int64_t lplane = U * D * ldk;               // [Re L | Im L]
-  const int64_t site = 2 * 4 * Dp * ldk;            // BT, AC
-  const int64_t ct = U * D * 4 * Dp;                // GEMM-T output
-  const int64_t tt = U * 2 * Dp * ldk;              // [Re T^T | Im T^T]
-  const int64_t cl = 4 * Dp * U * 2 * Dp;           // GEMM-C output
-  const int64_t pad = 64;                           // 16-byte alignment of each part
-  return (size_t)(lplane + site + ct + tt + cl + 8 * pad);
+  const int64_t D = chi, Dp = chi, U = max_nodes;
+  const int64_t site = 4 * Dp * 2 * D + 2 * Dp * 4 * D;   // BT, A2
+  const int64_t w = U * Dp * 4 * D;                       // W rows of up to U children
+  const int64_t cl = 2 * Dp * U * Dp;                     // GEMM-C output
+  const int64_t pad = 64;                                 // 256-byte alignment of each part
+  return (size_t)(site + w + cl + 4 * pad);
 }
 
 namespace {
 struct Parts {
-  float *lp, *bt, *ac, *ct, *tt, *cl;
+  float *bt, *a2, *w, *cl;
 };
 Parts carve(float* base, int chi, int max_nodes) {
-  const int64_t D = chi, Dp = chi, U = max_nodes, ldk = round4(2 * D);
+  const int64_t D = chi, Dp = chi, U = max_nodes;
   auto take = [&](int64_t n) {
     float* p = base;
     base += (n + 63) & ~(int64_t)63;
     return p;
   };
   Parts p;
-  p.lp = take(U * D * ldk);
-  p.bt = take(4 * Dp * ldk);
-  p.ac = take(4 * Dp * ldk);
-  p.ct = take(U * D * 4 * Dp);
-  p.tt = take(U * 2 * Dp * ldk);
-  p.cl = take(4 * Dp * U * 2 * Dp);
+  p.bt = take(4 * Dp * 2 * D);
+  p.a2 = take(2 * Dp * 4 * D);
+  p.w = take(U * Dp * 4 * D);
+  p.cl = take(2 * Dp * U * Dp);
   return p;
 }
 }  // namespace
 
 cudaError_t env_tc_site(const EnvTc& s, const Cx<float>* Bk, int D, int Dp, cudaStream_t st) {
   const Parts p = carve(s.scratch, s.chi, s.max_nodes);
-  const int64_t ldk = round4(2 * D);
-  k_tc_site_operands<<<grid_for(4 * Dp * ldk), 256, 0, st>>>(Bk, D, Dp, ldk, p.bt, p.ac);
+  k_tc_site_operands<<<grid_for(16 * (int64_t)Dp * D), 256, 0, st>>>(Bk, D, Dp, p.bt, p.a2);
   return cudaGetLastError();
 }
 
@@ -197,36 +158,31 @@ cudaError_t env_tc_T(const EnvTc& s, const Cx<float>* L, Cx<float>* T, int U, in
                      cudaEvent_t e0, cudaEvent_t e1) {
   if (U <= 0) return cudaSuccess;
   const Parts p = carve(s.scratch, s.chi, s.max_nodes);
-  const int64_t ldk = round4(2 * D), chi2 = (int64_t)s.chi * s.chi;
-  k_tc_pack_L<<<grid_for((int64_t)U * D * ldk), 256, 0, st>>>(L, chi2, U, D, p.lp, ldk);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   if (e0 && (e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
-  e = tc::launch_gemm_tf32x3(tc::Plane{p.lp, ldk}, tc::Plane{p.bt, ldk}, U * D, 4 * Dp, 2 * D, p.ct, 4 * Dp, s.err,
-                             st);
+  e = tc::launch_gemm_tf32x3(tc::Plane{(const float*)L, 2 * (int64_t)D}, tc::Plane{p.bt, 2 * (int64_t)D}, U * D,
+                             4 * Dp, 2 * D, (float*)T, 4 * (int64_t)Dp, s.err, st);
   if (e != cudaSuccess) return e;
   if (e1 && (e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
-  k_tc_scatter_T<<<grid_for((int64_t)U * 2 * D * Dp), 256, 0, st>>>(p.ct, U, D, Dp, T, chi2);
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
-cudaError_t env_tc_children(const EnvTc& s, const Cx<float>* T, int pa, int pb, int D, int Dp,
-                            const int32_t* parent, const uint8_t* edge, int nc, int node_base, Cx<float>* Lout,
-                            cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
-  if (nc <= 0 || pb <= pa) return cudaSuccess;
+cudaError_t env_tc_children(const EnvTc& s, const Cx<float>* T, const int32_t* parent, const uint8_t* edge, int nc,
+                            int node_base, int D, int Dp, Cx<float>* Lout, cudaStream_t st, cudaEvent_t e0,
+                            cudaEvent_t e1) {
+  if (nc <= 0) return cudaSuccess;
   const Parts p = carve(s.scratch, s.chi, s.max_nodes);
-  const int64_t ldk = round4(2 * D), chi2 = (int64_t)s.chi * s.chi;
-  const int np = pb - pa;
-  k_tc_pack_TT<<<dim3((Dp + 31) / 32, (D + 31) / 32, np * 2), dim3(32, 8), 0, st>>>(T, chi2, pa, D, Dp, p.tt, ldk);
+  k_tc_pack_W<<<dim3((Dp + 31) / 32, (D + 31) / 32, nc), dim3(32, 8), 0, st>>>(T, parent, edge, node_base, D, Dp,
+                                                                               p.w);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int64_t N = (int64_t)np * 2 * Dp;
+  const int64_t N = (int64_t)nc * Dp;
   if (e0 && (e = cudaEventRecord(e0, st)) != cudaSuccess) return e;
-  e = tc::launch_gemm_tf32x3(tc::Plane{p.ac, ldk}, tc::Plane{p.tt, ldk}, 4 * Dp, (int)N, 2 * D, p.cl, N, s.err, st);
+  e = tc::launch_gemm_tf32x3(tc::Plane{p.a2, 4 * (int64_t)D}, tc::Plane{p.w, 4 * (int64_t)D}, 2 * Dp, (int)N, 4 * D,
+                             p.cl, N, s.err, st);
   if (e != cudaSuccess) return e;
   if (e1 && (e = cudaEventRecord(e1, st)) != cudaSuccess) return e;
-  k_tc_combine<<<grid_for((int64_t)nc * Dp * Dp), 256, 0, st>>>(p.cl, N, Dp, parent, edge, nc, node_base, pa, Lout,
-                                                                chi2);
+  k_tc_place<<<grid_for((int64_t)nc * Dp * Dp), 256, 0, st>>>(p.cl, Dp, nc, Lout);
   return cudaGetLastError();
 }
 

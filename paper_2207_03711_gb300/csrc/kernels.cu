@@ -136,12 +136,12 @@ __device__ void block_gemm(int Mdim, int Ndim, int K, const GemmTerm<R>* terms, 
 }
 
 // The same product spread over a grid: one 64 x 64 tile per thread block, blockIdx.z
-// selecting one of up to two independent products.
+// selecting one of up to four independent products.
 template <class R>
 struct GridGemm {
-  GemmTerm<R> t[2][2];
+  GemmTerm<R> t[4][2];
   int nterm;
-  Cx<R>* C[2];
+  Cx<R>* C[4];
   int ldc, M, N, K;
 };
 
@@ -751,7 +751,7 @@ cudaError_t launch_circuit(const DevMPS& m, int prec, const CircDev& c, int64_t 
 // (ranks[k] = left dimension of site k).
 template <class R>
 static cudaError_t right_envs_t(const DevMPS& m, int slot, const int* ranks, const int64_t* site_off, Cx<R>* Renv,
-                                Cx<R>* Bhat, cudaStream_t st) {
+                                Cx<R>* Bhat, Cx<R>* Q, cudaStream_t st) {
   const int n = m.n;
   const size_t chi2 = (size_t)m.chi * m.chi;
   const Cx<R>* Bslot = (const Cx<R>*)m.B + (size_t)slot * m.slot_elems;
@@ -784,16 +784,39 @@ static cudaError_t right_envs_t(const DevMPS& m, int slot, const int* ranks, con
     for (int i = 0; i < 2; ++i) h.t[0][i] = GemmTerm<R>{Bh + i * Dr, 2 * Dr, false, Bk + i * Dr, 2 * Dr, cx<R>(1, 0), true, true};
     h.C[0] = Renv + (size_t)k * chi2;
     k_cgemm_grid<R><<<dim3((Dl + 63) / 64, (Dl + 63) / 64, 1), 256, 0, st>>>(h);
+    // Q_k^P = sum over the letter's two entries (i, j, s) of conj(s) Bhat^i (B^j)^+, one
+    // product per letter I, X, Y, Z: a string closing at site k with letter P has
+    // <P> = sum_ab L[a][b] conj(Q_k^P[a][b]) (Eq. 11 with the right part contracted)
+    GridGemm<R> q{};
+    q.nterm = 2;
+    q.ldc = Dl;
+    q.M = Dl;
+    q.N = Dl;
+    q.K = Dr;
+    for (int l = 0; l < 4; ++l) {
+      const int ii[4][2] = {{0, 1}, {0, 1}, {0, 1}, {0, 1}};
+      const int jj[4][2] = {{0, 1}, {1, 0}, {1, 0}, {0, 1}};
+      // conj of the letter's entries: I (1, 1), X (1, 1), Y (-i, i) -> (i, -i), Z (1, -1)
+      const Cx<R> cs[4][2] = {{cx<R>(1, 0), cx<R>(1, 0)},
+                              {cx<R>(1, 0), cx<R>(1, 0)},
+                              {cx<R>(0, 1), cx<R>(0, -1)},
+                              {cx<R>(1, 0), cx<R>(-1, 0)}};
+      for (int e = 0; e < 2; ++e)
+        q.t[l][e] = GemmTerm<R>{Bh + ii[l][e] * Dr, 2 * Dr, false, Bk + jj[l][e] * Dr, 2 * Dr, cs[l][e], true, true};
+      q.C[l] = Q + ((size_t)k * 4 + l) * chi2;
+    }
+    k_cgemm_grid<R><<<dim3((Dl + 63) / 64, (Dl + 63) / 64, 4), 256, 0, st>>>(q);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, const int* ranks, const int64_t* site_off,
                               MeasDev& w, cudaStream_t st, int* launches) {
-  *launches += 2 * m.n;
+  *launches += 3 * m.n;
   if (prec == MPS_PREC_FP64)
-    return right_envs_t<double>(m, slot, ranks, site_off, (Cx<double>*)w.R, (Cx<double>*)w.Bhat, st);
-  return right_envs_t<float>(m, slot, ranks, site_off, (Cx<float>*)w.R, (Cx<float>*)w.Bhat, st);
+    return right_envs_t<double>(m, slot, ranks, site_off, (Cx<double>*)w.R, (Cx<double>*)w.Bhat, (Cx<double>*)w.Q,
+                                st);
+  return right_envs_t<float>(m, slot, ranks, site_off, (Cx<float>*)w.R, (Cx<float>*)w.Bhat, (Cx<float>*)w.Q, st);
 }
 
 // ------------------------------------------------------------------ trie level
@@ -808,18 +831,19 @@ __device__ __forceinline__ void letter_entries(uint8_t l, int* ii, int* jj, Cx<R
   }
 }
 
+// Level buffers are dense: node u of level k holds L at u Dk^2 (leading dimension Dk)
+// and, on the CUDA-core route, T_j at (2u + j) Dk Dk1 (leading dimension Dk1).
 // T_j[u] = L_k[u] B_k^j  (Dk x Dk)(Dk x Dk1), grid (nodes, 2)
 template <class R>
 __global__ void __launch_bounds__(256) k_level_T(DevMPS m, int slot, int k, const Cx<R>* Lin, Cx<R>* T) {
   __shared__ Cx<R> As[64][17];
   __shared__ Cx<R> Bs[16][65];
   const int u = blockIdx.x, j = blockIdx.y;
-  const int chi2 = m.chi * m.chi;
   const int* rank = m.rank + (size_t)slot * (m.n + 1);
   const int Dk = rank[k], Dk1 = rank[k + 1];
   const Cx<R>* Bk = (const Cx<R>*)m.B + (size_t)slot * m.slot_elems + m.site_off[k];
-  GemmTerm<R> t{Lin + (size_t)u * chi2, Dk, false, Bk + j * Dk1, 2 * Dk1, cx<R>(1, 0), false};
-  block_gemm<R, 256>(Dk, Dk1, Dk, &t, 1, T + ((size_t)u * 2 + j) * chi2, Dk1, As, Bs);
+  GemmTerm<R> t{Lin + (size_t)u * Dk * Dk, Dk, false, Bk + j * Dk1, 2 * Dk1, cx<R>(1, 0), false};
+  block_gemm<R, 256>(Dk, Dk1, Dk, &t, 1, T + ((size_t)u * 2 + j) * Dk * Dk1, Dk1, As, Bs);
 }
 
 // L_{k+1}[c] = sum_ij sigma_ij (B_k^i)^+ T_j[parent(c)]
@@ -830,7 +854,6 @@ __global__ void __launch_bounds__(256) k_level_child(DevMPS m, int slot, int k, 
   __shared__ Cx<R> As[64][17];
   __shared__ Cx<R> Bs[16][65];
   const int c = blockIdx.x;
-  const int chi2 = m.chi * m.chi;
   const int* rank = m.rank + (size_t)slot * (m.n + 1);
   const int Dk = rank[k], Dk1 = rank[k + 1];
   const Cx<R>* Bk = (const Cx<R>*)m.B + (size_t)slot * m.slot_elems + m.site_off[k];
@@ -840,40 +863,46 @@ __global__ void __launch_bounds__(256) k_level_child(DevMPS m, int slot, int k, 
   letter_entries<R>(edge[c], ii, jj, sg);
   GemmTerm<R> t[2];
   for (int e = 0; e < 2; ++e)
-    t[e] = GemmTerm<R>{Bk + ii[e] * Dk1, 2 * Dk1, true, T + ((size_t)u * 2 + jj[e]) * chi2, Dk1, sg[e], false};
-  block_gemm<R, 256>(Dk1, Dk1, Dk, t, 2, Lout + (size_t)c * chi2, Dk1, As, Bs);
+    t[e] = GemmTerm<R>{Bk + ii[e] * Dk1, 2 * Dk1, true, T + ((size_t)u * 2 + jj[e]) * Dk * Dk1, Dk1, sg[e], false};
+  block_gemm<R, 256>(Dk1, Dk1, Dk, t, 2, Lout + (size_t)c * Dk1 * Dk1, Dk1, As, Bs);
 }
 
-// <P> (unnormalised) = sum_ij sigma_ij <Bhat_k^i, T_j[node]>_F, FP64 accumulation
+// <P> (unnormalised) of a string closing at site k with letter P on node u:
+// sum_ab L[u][a][b] conj(Q_k^P[a][b]), Q_k^P = sum_ij conj(P_ij) Bhat_k^i (B_k^j)^+ from the
+// right-environment pass. This equals sum_ij P_ij <Bhat_k^i, L[u] B_k^j>_F (Eq. 11 with
+// the right part contracted first) and reads one D x D block of the node instead of the
+// two D x D' blocks of T. Both blocks are contiguous with leading dimension D.
 template <class R>
 __global__ void __launch_bounds__(256) k_level_close(DevMPS m, int slot, int k, const int32_t* cnode,
                                                      const uint8_t* cletter, const int32_t* cterm,
-                                                     const Cx<R>* T, const Cx<R>* Bhat, double* vals,
+                                                     const Cx<R>* L, const Cx<R>* Q, double* vals,
                                                      int node_base) {
   __shared__ double red[2][8];
   const int c = blockIdx.x;
   const int chi2 = m.chi * m.chi;
   const int* rank = m.rank + (size_t)slot * (m.n + 1);
-  const int Dk = rank[k], Dk1 = rank[k + 1];
-  const Cx<R>* Bh = Bhat + m.site_off[k];
-  const int u = cnode[c] - node_base;
-  int ii[2], jj[2];
-  Cx<R> sg[2];
-  letter_entries<R>(cletter[c], ii, jj, sg);
+  const int Dk = rank[k];
+  const Cx<R>* Lu = L + (size_t)(cnode[c] - node_base) * Dk * Dk;
+  const Cx<R>* Qp = Q + ((size_t)k * 4 + (cletter[c] & 3)) * chi2;
+  const int n = Dk * Dk;
   double re = 0.0, im = 0.0;
-  for (int e = 0; e < 2; ++e) {
-    const Cx<R>* Tj = T + ((size_t)u * 2 + jj[e]) * chi2;
-    double pr = 0.0, pi = 0.0;
-    for (int idx = threadIdx.x; idx < Dk * Dk1; idx += 256) {
-      const int a = idx / Dk1, b = idx - a * Dk1;
-      const Cx<R> h = Bh[(size_t)(2 * a + ii[e]) * Dk1 + b];
-      const Cx<R> tv = Tj[idx];
-      // conj(h) * tv
-      pr += (double)h.x * tv.x + (double)h.y * tv.y;
-      pi += (double)h.x * tv.y - (double)h.y * tv.x;
+  int idx = threadIdx.x;
+  while (idx < n) {
+    // R = float: FP32 products summed in FP32 over runs of 8 entries, the runs summed in
+    // FP64. GB300's FP64 (and FP32 -> FP64 conversion) throughput is a small fraction of
+    // its FP32 rate; one FP64 step per entry made the close a third of a chi = 256
+    // measurement. A run's FP32 sum is off by at most ~8 ulps of its magnitudes, below
+    // the ~2^-21 relative error of the tensor-core environments. R = double: FP64.
+    R sr = 0, si = 0;
+#pragma unroll 4
+    for (int t = 0; t < 8 && idx < n; ++t, idx += 256) {
+      const Cx<R> q = Qp[idx], l = Lu[idx];
+      // conj(q) * l
+      sr += q.x * l.x + q.y * l.y;
+      si += q.x * l.y - q.y * l.x;
     }
-    re += (double)sg[e].x * pr - (double)sg[e].y * pi;
-    im += (double)sg[e].x * pi + (double)sg[e].y * pr;
+    re += (double)sr;
+    im += (double)si;
   }
   for (int o = 16; o > 0; o >>= 1) {
     re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -905,16 +934,16 @@ cudaError_t launch_env_T(const DevMPS& m, int prec, int slot, int k, const void*
   return cudaGetLastError();
 }
 
-cudaError_t launch_env_close(const DevMPS& m, int prec, int slot, int k, const void* T, const void* Bhat,
+cudaError_t launch_env_close(const DevMPS& m, int prec, int slot, int k, const void* L, const void* Q,
                              const int32_t* cnode, const uint8_t* cletter, const int32_t* cterm, int n_closes,
                              int node_base, double* vals, cudaStream_t st) {
   if (n_closes <= 0) return cudaSuccess;
   if (prec == MPS_PREC_FP64)
-    k_level_close<double><<<n_closes, 256, 0, st>>>(m, slot, k, cnode, cletter, cterm, (const Cx<double>*)T,
-                                                     (const Cx<double>*)Bhat, vals, node_base);
+    k_level_close<double><<<n_closes, 256, 0, st>>>(m, slot, k, cnode, cletter, cterm, (const Cx<double>*)L,
+                                                     (const Cx<double>*)Q, vals, node_base);
   else
-    k_level_close<float><<<n_closes, 256, 0, st>>>(m, slot, k, cnode, cletter, cterm, (const Cx<float>*)T,
-                                                    (const Cx<float>*)Bhat, vals, node_base);
+    k_level_close<float><<<n_closes, 256, 0, st>>>(m, slot, k, cnode, cletter, cterm, (const Cx<float>*)L,
+                                                    (const Cx<float>*)Q, vals, node_base);
   return cudaGetLastError();
 }
 

@@ -61,6 +61,7 @@ cudaError_t launch_circuit(const DevMPS& m, int prec, const CircDev& c, int64_t 
 struct MeasDev {
   void* R;          // complex<R> [n+1][chi*chi] right identity environments R_k
   void* Bhat;       // complex<R> like one slot of B: B_k^i R_{k+1}
+  void* Q;          // complex<R> [n][4][chi*chi]: Q_k^P = sum_ij conj(P_ij) Bhat_k^i (B_k^j)^+ per letter P
   double* vals;     // [n_terms][2] re, im of unnormalised <P>
   double* out;      // [4 + n_terms*2]: E, norm, ...
 };
@@ -79,7 +80,7 @@ cudaError_t launch_right_envs(const DevMPS& m, int prec, int slot, const int* ra
 // parent are absolute trie indices; node_base is the trie index of buffer entry 0.
 cudaError_t launch_env_T(const DevMPS& m, int prec, int slot, int k, const void* L, void* T, int n_nodes,
                          cudaStream_t st);
-cudaError_t launch_env_close(const DevMPS& m, int prec, int slot, int k, const void* T, const void* Bhat,
+cudaError_t launch_env_close(const DevMPS& m, int prec, int slot, int k, const void* L, const void* Q,
                              const int32_t* cnode, const uint8_t* cletter, const int32_t* cterm, int n_closes,
                              int node_base, double* vals, cudaStream_t st);
 cudaError_t launch_env_child(const DevMPS& m, int prec, int slot, int k, const void* T, const int32_t* parent,
