@@ -886,18 +886,34 @@ __global__ void __launch_bounds__(256) k_level_close(DevMPS m, int slot, int k, 
   const Cx<R>* Qp = Q + ((size_t)k * 4 + (cletter[c] & 3)) * chi2;
   const int n = Dk * Dk;
   double re = 0.0, im = 0.0;
+  // R = float: FP32 products summed in FP32 over runs of 8 entries, the runs summed in
+  // FP64. GB300's FP64 (and FP32 -> FP64 conversion) throughput is a small fraction of
+  // its FP32 rate; one FP64 step per entry made the close a third of a chi = 256
+  // measurement. A run's FP32 sum is off by at most ~8 ulps of its magnitudes, below the
+  // ~2^-21 relative error of the tensor-core environments. R = double: FP64.
   int idx = threadIdx.x;
-  while (idx < n) {
-    // R = float: FP32 products summed in FP32 over runs of 8 entries, the runs summed in
-    // FP64. GB300's FP64 (and FP32 -> FP64 conversion) throughput is a small fraction of
-    // its FP32 rate; one FP64 step per entry made the close a third of a chi = 256
-    // measurement. A run's FP32 sum is off by at most ~8 ulps of its magnitudes, below
-    // the ~2^-21 relative error of the tensor-core environments. R = double: FP64.
+  for (; idx + 7 * 256 < n; idx += 8 * 256) {
+    // a full run: its 16 loads are issued before the products that use them
+    Cx<R> q[8], l[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      q[t] = Qp[idx + t * 256];
+      l[t] = Lu[idx + t * 256];
+    }
     R sr = 0, si = 0;
-#pragma unroll 4
-    for (int t = 0; t < 8 && idx < n; ++t, idx += 256) {
-      const Cx<R> q = Qp[idx], l = Lu[idx];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
       // conj(q) * l
+      sr += q[t].x * l[t].x + q[t].y * l[t].y;
+      si += q[t].x * l[t].y - q[t].y * l[t].x;
+    }
+    re += (double)sr;
+    im += (double)si;
+  }
+  if (idx < n) {
+    R sr = 0, si = 0;
+    for (; idx < n; idx += 256) {
+      const Cx<R> q = Qp[idx], l = Lu[idx];
       sr += q.x * l.x + q.y * l.y;
       si += q.x * l.y - q.y * l.x;
     }
