@@ -295,7 +295,9 @@ static MeasPlan meas_plan(const Trie& t, int chi, size_t es, bool mixed, size_t 
     // a quarter of an explicit budget, else 1 GiB (chi <= 128) or 4 GiB
     const size_t tc_budget = explicit_budget ? std::max<size_t>(size_t(64) << 20, budget / 4)
                                              : (chi <= 128 ? size_t(1) : size_t(4)) << 30;
-    p.tc_nodes = (int)std::min<size_t>((size_t)cmax, std::max<size_t>(32, tc_budget / per_node));
+    // at most 65 535 children per chunk: the W-row kernel puts one child per grid z index
+    p.tc_nodes = (int)std::min<size_t>(std::min<size_t>((size_t)cmax, 65535),
+                                       std::max<size_t>(32, tc_budget / per_node));
     p.tc_bytes = env_tc_scratch_floats(chi, p.tc_nodes) * sizeof(float) + 256;
   }
   return p;
