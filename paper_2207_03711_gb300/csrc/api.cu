@@ -478,7 +478,9 @@ static int meas_chunk(MeasWalk& c, int k, int u0, int u1) {
   const int U = u1 - u0, D = c.r[k], Dp = c.r[k + 1];
   void* L = m->lvl_L[k];
   void* T = m->lvl_T[k];
-  const bool tc = m->prec == MPS_MIXED && m->tc.scratch && D >= kTcMinDim && Dp >= kTcMinDim;
+  // the tensor-core route reads L in place as rows of 2D floats, which TMA needs 16-byte
+  // aligned: levels with an odd left bond stay on the CUDA-core kernels
+  const bool tc = m->prec == MPS_MIXED && m->tc.scratch && D >= kTcMinDim && Dp >= kTcMinDim && (D & 1) == 0;
   if (tc) {
     const Cx<float>* Bk = (const Cx<float>*)m->dm.B + (size_t)c.slot * m->dm.slot_elems + m->site_off[k];
     CU(env_tc_site(m->tc, Bk, D, Dp, m->st));

@@ -151,3 +151,32 @@ def test_chi256_measurement_64q(prec):
     with pytest.raises(G.MpsError) as e:       # gates are applied at chi <= 128 only
         G.mps_apply_gates(M, np.array([0], dtype=np.int32), np.eye(4)[None].astype(complex))
     assert e.value.code == G.MPS_EINVAL
+
+
+def test_ragged_odd_bonds_chi256():
+    """A loaded chi = 256 state whose bond ranks are odd where both bonds of a level reach
+    128: an odd right bond runs on the tensor cores (GEMM widths, leading dimensions and T
+    rows of odd width), an odd left bond goes to the CUDA-core kernels (the tensor-core
+    route reads L in place as 16-byte-aligned rows of 2D floats); both precisions agree
+    with the oracle."""
+    n, chi = 18, 256
+    r = [2, 4, 8, 16, 32, 64, 128, 255, 131, 201, 128, 64, 32, 16, 8, 4, 2]
+    g = syn.random_mps_gaussians(n, r, 21)
+    rr = [1] + r + [1]
+    for k in range(n):
+        g[k][:rr[k + 1]] *= 2.0
+    st = mps.random_canonical(n, r, g)
+    codes = jw_shaped_strings(n, 60, 22)
+    ref = np.array([mps.expect_string(st, c) for c in codes]) / mps.norm2(st)
+    for prec, tol in ((G.MPS_FP64, 1e-10), (G.MPS_MIXED, 2e-5)):
+        M = G.mps_create(n, chi, prec)
+        G.mps_set_state(M, st.B, st.lam)
+        assert list(G.mps_get_ranks(M)) == r
+        G.mps_set_kernel_timing(M, True)
+        vals = G.mps_expect_paulis(M, codes)
+        s = G.mps_get_stats(M)
+        err = np.abs(vals - ref).max()
+        print(f"18q chi256 odd bonds prec={prec}: max|d<P>| = {err:.3e}, tc launches {s['tc_gemm_launches']}")
+        if prec == G.MPS_MIXED:
+            assert s["tc_gemm_launches"] > 0
+        assert err <= tol
