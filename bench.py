@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--config4-tc-case", action="store_true",
                     help="small profiling case of the tensor-core GEMM: one 64-qubit chi=256 measurement of "
                          "the first --case-strings strings")
+    ap.add_argument("--tc-gemm-case", action="store_true",
+                    help="small profiling case: one environment-shaped tensor-core GEMM through the C ABI")
     ap.add_argument("--config3", action="store_true",
                     help="256 parameter-shift circuits of a 32-qubit chi=128 ansatz per step (one gradient)")
     ap.add_argument("--random-gates", action="store_true",
@@ -550,6 +552,32 @@ def run_config4(args):
     print(json.dumps(line))
 
 
+def run_tc_gemm_case():
+    """A fixed launch for ncu: one 43 520 x 1024 x 512 tensor-core GEMM (the GEMM-T shape of
+    a 170-node chunk at D = D' = 256) through the C-ABI entry on aligned random operands,
+    three calls; prints the CUDA-event time of the last call."""
+    import torch
+    import paper_2207_03711_gb300 as G
+    G.build()
+    G.load_library()
+    M, N, K = 43520, 1024, 512
+    g = torch.Generator(device="cuda").manual_seed(SEED)
+    A = torch.randn(M, K, device="cuda", generator=g)
+    B = torch.randn(N, K, device="cuda", generator=g)
+    C = torch.empty(M, N, device="cuda")
+    for _ in range(2):
+        G.mps_tc_gemm_tf32x3(M, N, K, A.data_ptr(), K, B.data_ptr(), K, C.data_ptr(), N)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    G.mps_tc_gemm_tf32x3(M, N, K, A.data_ptr(), K, B.data_ptr(), K, C.data_ptr(), N)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"tc_gemm_case": True, "M": M, "N": N, "K": K, "ms_call": ms,
+                      "tflops_algorithmic": 2.0 * M * N * K / ms / 1e9}))
+
+
 def run_config4_tc_case(n_strings, budget_mb=0):
     """A short fixed workload for ncu: one chi = 256 measurement of the first n_strings
     strings of the 64-qubit Hamiltonian (mixed precision)."""
@@ -792,6 +820,8 @@ def main():
         run_config3(args)
     elif args.config4_tc_case:
         run_config4_tc_case(args.case_strings, args.case_budget_mb)
+    elif args.tc_gemm_case:
+        run_tc_gemm_case()
     elif args.profile_case:
         run_profile_case()
     elif args.impl == "reference":

@@ -96,13 +96,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait on the phase with the given parity; false (and *err set) on time-out.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+// backoff: the many-thread waiters (split and epilogue warps) sleep briefly between
+// polls, so that their polling does not take shared-memory bandwidth from the split and
+// the TMA writes; the single-thread producer and MMA issuer poll without sleeping.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code,
+                                          bool backoff = false) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (clock64() - t0 > kWaitCycles) {
       atomicExch(err, code);
       return false;
     }
+    if (backoff) __nanosleep(64);
   }
   return true;
 }
@@ -241,7 +246,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int ct = tid - CONV_WARP0 * 32;
     for (int g = 0; g < total; ++g) {
       const int s = g % STAGES;
-      const bool got = mbar_wait(smem_u32(&full[s]), (g / STAGES) & 1, err, 5);
+      const bool got = mbar_wait(smem_u32(&full[s]), (g / STAGES) & 1, err, 5, true);
       // all split threads leave together if any wait ran out (none is left at a barrier)
       uint32_t all_ok;
       asm volatile(
@@ -328,7 +333,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int kt = 0; kt < nk && ok; ++kt, ++g) {
         const int b = g & 1;
         // tcgen05.ld is warp-collective: the whole warp goes on or stops together
-        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ready[b]), (g >> 1) & 1, err, 3));
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ready[b]), (g >> 1) & 1, err, 3, true));
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (ok) {
 #pragma unroll
