@@ -247,10 +247,12 @@ def test_prefix_parity_24q(prec, chi, ng):
             assert np.abs(a - b).max() <= 1e-10
         assert np.abs(ev_g - ev_o).max() <= 1e-9
     else:
-        # FP32 SVDs inside a truncated chain: differences stay in the chaos band that
-        # FP64-vs-FP64 rounding changes already produce: a 1e-15 relative change of every
-        # M' moves truncated-chain energies by ~1e-2 Ha at 16 qubits, chi = 32
-        assert np.abs(ev_g - ev_o).max() <= 2e-3
+        # FP32 SVDs inside a truncated chain: over a long chain the differences grow into
+        # the chaos band that FP64-vs-FP64 rounding changes already produce (a 1e-15
+        # relative change of every M' moves truncated-chain energies by ~1e-2 Ha at 16
+        # qubits, chi = 32); over these first 3000 gates they are still small (1.8e-6
+        # measured on a GB300), and the bound keeps a wide margin above that
+        assert np.abs(ev_g - ev_o).max() <= 1e-4
 
 
 # ----------------------------------------------------------------- edge cases
