@@ -213,3 +213,40 @@ def test_injected_allocation_failure_midway(monkeypatch, after):
     monkeypatch.delenv("MPS_FAULT_ALLOC_AFTER")
     M = G.mps_create(8, 16, G.MPS_MIXED, n_slots=2)
     M.close()
+
+
+def test_ladder_cancellation_reorders_only_commuting_runs():
+    """circ_cancel_ladders reorders a run of rotations that share a parameter only if all
+    of its strings commute pairwise, never across parameters and never fixed-angle
+    rotations (parameter < 0); a run is sorted by its letters from the lowest
+    non-identity site up."""
+    n = 4
+    X, Y, Z = 1, 2, 3
+    rots = [
+        ([Y, X, 0, 0], 0, 1.0), ([X, Y, 0, 0], 0, -1.0),     # commuting run: reordered (X < Y)
+        ([X, 0, 0, 0], 1, 1.0), ([Z, 0, 0, 0], 1, 1.0),      # anticommuting run: kept
+        ([0, Y, Z, 0], -1, 0.3), ([0, X, Z, 0], -1, 0.2),    # fixed angles: kept
+        ([0, 0, Y, X], 2, 1.0),                              # run of one
+    ]
+    P = np.array([r[0] for r in rots], dtype=np.uint8)
+    pidx = np.array([r[1] for r in rots], dtype=np.int32)
+    scale = np.array([r[2] for r in rots])
+    C = G.circ_create(P, pidx, scale)
+    theta = np.array([0.3, -0.7, 0.5])
+    b0, U0 = G.circ_export_gates(C, theta)
+    G.circ_cancel_ladders(C)
+    P2, pidx2, scale2 = G.circ_get_rotations(C)
+    assert P2[0].tolist() == [X, Y, 0, 0] and scale2[0] == -1.0
+    assert P2[1].tolist() == [Y, X, 0, 0] and scale2[1] == 1.0
+    assert np.array_equal(P2[2:], P[2:]) and np.array_equal(pidx2, pidx) and np.array_equal(scale2[2:], scale[2:])
+    # the same unitary: both gate lists applied to a random state agree
+    rng = np.random.default_rng(0)
+    psi0 = rng.normal(size=2 ** n) + 1j * rng.normal(size=2 ** n)
+    b1, U1 = G.circ_export_gates(C, theta)
+    outs = []
+    for bonds, Us in ((b0, U0), (b1, U1)):
+        psi = psi0.copy()
+        for b, U in zip(bonds, Us):
+            psi = circuit.apply_two_site_sv(psi, int(b), U, n)
+        outs.append(psi)
+    assert np.abs(outs[0] - outs[1]).max() <= 1e-12
