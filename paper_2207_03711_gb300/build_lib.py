@@ -41,7 +41,9 @@ def build(force=False, verbose=False):
     nvcc = _nvcc()
     inc = ["-I", CSRC, "-I", os.path.join(ROOT, "include")]
     jobs = [
-        ["g++", "-O2", "-fPIC", "-std=c++17", "-Wall", *inc, "-c", os.path.join(CSRC, "host.cpp"),
+        # no FMA contraction: the host arithmetic rounds the same on x86-64 and aarch64
+        ["g++", "-O2", "-fPIC", "-std=c++17", "-Wall", "-pthread", "-ffp-contract=off", *inc, "-c",
+         os.path.join(CSRC, "host.cpp"),
          "-o", os.path.join(OBJ, "host.o")],
     ]
     for name in ("kernels", "api", "tc_gemm", "env_tc"):
@@ -55,7 +57,7 @@ def build(force=False, verbose=False):
     tmp = LIB + ".tmp"
     _run([nvcc, *ARCH, "-shared", "-o", tmp, os.path.join(OBJ, "host.o"), os.path.join(OBJ, "kernels.o"),
           os.path.join(OBJ, "api.o"), os.path.join(OBJ, "tc_gemm.o"),
-          os.path.join(OBJ, "env_tc.o")])
+          os.path.join(OBJ, "env_tc.o"), "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

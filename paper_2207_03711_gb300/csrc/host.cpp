@@ -14,6 +14,9 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <functional>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -98,31 +101,71 @@ static void add_ladder_product(const int* p, const bool* dag, int m, cd weight, 
   }
 }
 
+// The same, each term into the map of its hash class (maps[hash % count]).
+static void add_ladder_product_sharded(const int* p, const bool* dag, int m, cd weight, XZMap* maps, int count) {
+  XZTerm br[4][2];
+  for (int j = 0; j < m; ++j) ladder(p[j], dag[j], br[j]);
+  XZHash hs;
+  for (int combo = 0; combo < (1 << m); ++combo) {
+    XZTerm t{XZ(), weight};
+    for (int j = 0; j < m; ++j) t = mul(t, br[j][(combo >> j) & 1]);
+    maps[hs(t.k) % (size_t)count][t.k] += t.c;
+  }
+}
+
 // Letter-form coefficient of an accumulated XZ term.
 static inline cd letter_coeff(const XZ& k, cd c) { return c * ipow(-popc2(k.x, k.z)); }
+
+// f(0) .. f(count - 1) on up to count threads (the calls must not depend on each other).
+static void parallel_for(int count, const std::function<void(int)>& f) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int nt = std::min(count, hw);
+  if (nt <= 1) {
+    for (int i = 0; i < count; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nt; ++t)
+    pool.emplace_back([&] {
+      for (int i = next++; i < count; i = next++) f(i);
+    });
+  for (auto& th : pool) th.join();
+}
 
 static bool trie_less(const std::vector<uint8_t>& a, const std::vector<uint8_t>& b) {
   return std::lexicographical_compare(a.begin(), a.end(), b.begin(), b.end());
 }
 
 std::vector<Term> canonical_terms(int n, std::vector<Term> terms, double rel_drop) {
-  std::map<std::vector<uint8_t>, double, decltype(&trie_less)> merged(&trie_less);
-  for (auto& t : terms) merged[t.code] += t.coeff;
+  // trie order (lexicographic in the letters); equal strings merged in input order
+  std::stable_sort(terms.begin(), terms.end(), [](const Term& a, const Term& b) { return trie_less(a.code, b.code); });
+  std::vector<Term> merged;
+  merged.reserve(terms.size());
+  for (auto& t : terms) {
+    if (!merged.empty() && merged.back().code == t.code)
+      merged.back().coeff += t.coeff;
+    else
+      merged.push_back(std::move(t));
+  }
   double mx = 0;
-  for (auto& kv : merged) mx = std::max(mx, std::fabs(kv.second));
+  for (auto& t : merged) mx = std::max(mx, std::fabs(t.coeff));
   std::vector<Term> out;
-  for (auto& kv : merged)
-    if (std::fabs(kv.second) > rel_drop * mx) out.push_back({kv.first, kv.second});
+  out.reserve(merged.size());
+  for (auto& t : merged)
+    if (std::fabs(t.coeff) > rel_drop * mx) out.push_back(std::move(t));
   (void)n;
-  return out;  // std::map iterates in trie order
+  return out;
 }
 
 std::vector<Term> jordan_wigner(int m, const double* h, const double* eri, double e_core,
                                 std::string* err) {
   const int n = 2 * m;
-  XZMap acc;
-  acc.reserve(1 << 16);
+  // Work is split into a fixed number of parts, whatever the machine's thread count, and
+  // merged in a fixed order, so the coefficients are the same bits on every machine.
+  constexpr int kParts = 16;
   // one-body: h_pq a+_p a_q, equal spins
+  XZMap one;
   for (int p = 0; p < n; ++p)
     for (int q = 0; q < n; ++q) {
       if ((p & 1) != (q & 1)) continue;
@@ -130,42 +173,83 @@ std::vector<Term> jordan_wigner(int m, const double* h, const double* eri, doubl
       if (w == 0.0) continue;
       int idx[2] = {p, q};
       bool dg[2] = {true, false};
-      add_ladder_product(idx, dg, 2, cd(w, 0), acc);
+      add_ladder_product(idx, dg, 2, cd(w, 0), one);
     }
-  // two-body: 1/2 (pq|rs) a+_p a+_r a_s a_q, spin(p)=spin(q), spin(r)=spin(s)
-  for (int p = 0; p < n; ++p)
-    for (int q = 0; q < n; ++q) {
+  one[XZ()] += cd(e_core, 0);
+  // two-body: 1/2 (pq|rs) a+_p a+_r a_s a_q, spin(p) = spin(q), spin(r) = spin(s). The
+  // operator for (r, s, p, q) is the same as for (p, q, r, s) (two swaps), so each
+  // unordered pair of (p, q) and (r, s) is expanded once with both weights; r = p
+  // (a+_p a+_p = 0) and s = q are skipped, so the two pairs never coincide.
+  auto eri_at = [&](int p, int q, int r, int s) {
+    return eri[(((size_t)(p / 2) * m + q / 2) * m + r / 2) * m + s / 2];
+  };
+  // part t accumulates the (p, q) pairs t, t + kParts, ... into kParts maps by key hash;
+  // shard s then merges map s of every part, in part order
+  std::vector<std::vector<XZMap>> part(kParts, std::vector<XZMap>(kParts));
+  auto run_part = [&](int t) {
+    XZMap* acc = part[t].data();
+    for (int pq = t; pq < n * n; pq += kParts) {
+      const int p = pq / n, q = pq % n;
       if ((p & 1) != (q & 1)) continue;
       for (int r = 0; r < n; ++r) {
-        if (r == p) continue;  // a+_p a+_p = 0
+        if (r == p) continue;
         for (int s = 0; s < n; ++s) {
-          if ((r & 1) != (s & 1) || s == q) continue;  // a_s a_s = 0
-          double w = eri[(((size_t)(p / 2) * m + q / 2) * m + r / 2) * m + s / 2];
+          if ((r & 1) != (s & 1) || s == q || r * n + s < pq) continue;
+          const double w = 0.5 * (eri_at(p, q, r, s) + eri_at(r, s, p, q));
           if (w == 0.0) continue;
           int idx[4] = {p, r, s, q};
           bool dg[4] = {true, true, false, false};
-          add_ladder_product(idx, dg, 4, cd(0.5 * w, 0), acc);
+          add_ladder_product_sharded(idx, dg, 4, cd(w, 0), acc, kParts);
         }
       }
     }
-  acc[XZ()] += cd(e_core, 0);
-  std::vector<Term> terms;
-  terms.reserve(acc.size());
-  double mx = 0;
-  for (auto& kv : acc) mx = std::max(mx, std::abs(kv.second));
-  for (auto& kv : acc) {
-    cd c = letter_coeff(kv.first, kv.second);
-    if (std::abs(c) <= 1e-12 * mx) continue;
-    if (std::fabs(c.imag()) > 1e-10 * std::max(1.0, mx)) {
-      if (err) *err = "Jordan-Wigner coefficient with an imaginary part: integrals not Hermitian";
-      return {};
+  };
+  std::vector<XZMap> shard(kParts);
+  std::vector<double> shard_max(kParts, 0.0);
+  auto run_shard = [&](int t) {
+    XZMap& out = shard[t];
+    XZHash hs;
+    for (auto& kv : one)
+      if (hs(kv.first) % kParts == (size_t)t) out[kv.first] += kv.second;
+    for (int c = 0; c < kParts; ++c) {
+      for (auto& kv : part[c][t]) out[kv.first] += kv.second;
+      XZMap().swap(part[c][t]);
     }
-    Term t;
-    t.code.resize(n);
-    xz_to_letters(kv.first, n, t.code.data());
-    t.coeff = c.real();
-    terms.push_back(std::move(t));
+    for (auto& kv : out) shard_max[t] = std::max(shard_max[t], std::abs(kv.second));
+  };
+  parallel_for(kParts, run_part);
+  parallel_for(kParts, run_shard);
+  const double mx = *std::max_element(shard_max.begin(), shard_max.end());
+  // letters and the relative drop, per shard; concatenated in shard order
+  std::vector<std::vector<Term>> found(kParts);
+  std::vector<int> bad(kParts, 0);
+  auto run_collect = [&](int t) {
+    for (auto& kv : shard[t]) {
+      cd c = letter_coeff(kv.first, kv.second);
+      if (std::abs(c) <= 1e-12 * mx) continue;
+      if (std::fabs(c.imag()) > 1e-10 * std::max(1.0, mx)) {
+        bad[t] = 1;
+        return;
+      }
+      Term term;
+      term.code.resize(n);
+      xz_to_letters(kv.first, n, term.code.data());
+      term.coeff = c.real();
+      found[t].push_back(std::move(term));
+    }
+    XZMap().swap(shard[t]);
+  };
+  parallel_for(kParts, run_collect);
+  if (*std::max_element(bad.begin(), bad.end())) {
+    if (err) *err = "Jordan-Wigner coefficient with an imaginary part: integrals not Hermitian";
+    return {};
   }
+  std::vector<Term> terms;
+  size_t total = 0;
+  for (auto& f : found) total += f.size();
+  terms.reserve(total);
+  for (auto& f : found)
+    for (auto& t : f) terms.push_back(std::move(t));
   return canonical_terms(n, std::move(terms), 1e-12);
 }
 
