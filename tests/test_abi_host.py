@@ -44,6 +44,15 @@ def test_jw_matches_oracle(m, seed):
     assert np.abs(C - Co).max() <= 1e-12
 
 
+def test_jw_is_deterministic():
+    """The transform runs in parallel over fixed parts merged in a fixed order: two calls
+    give the same strings and the same coefficient bits."""
+    h, g = syn.random_integrals(10, 4)
+    P1, C1 = G.ham_get_terms(G.ham_jw_from_integrals(h, g))
+    P2, C2 = G.ham_get_terms(G.ham_jw_from_integrals(h, g))
+    assert np.array_equal(P1, P2) and np.array_equal(C1, C2)
+
+
 def test_h2_shaped_has_15_terms():
     h, g = syn.h2_shaped_integrals(1)
     assert G.ham_get_terms(G.ham_jw_from_integrals(h, g))[0].shape[0] == 15
